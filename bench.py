@@ -1,0 +1,370 @@
+#!/usr/bin/env python3
+"""Decoded Mbit/s of the GB300 layered BP syndrome decoder (arXiv 2004.09084).
+
+Workload (default): the rate-0.1 QC-MET-LDPC stand-in code with Z = 12500
+(n = 10^6), 128 codewords per GPU of random bits with syndromes s = Hx, BIAWGN
+channel LLRs at SNR 0.161, 100 layered iterations, no early termination.  A
+step is one full decode of the 128 codewords (one kernel launch).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank decodes its own 128 codewords (frames are
+independent: weak scaling, no collective on the data path); the step time is
+the maximum over ranks.  ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "decoded Mbit/s (128x1e6-bit codewords, fixed iters) and FER vs plain FP32 BP"
+RATE = "0.1"
+Z = 12500
+K_FRAMES = 128
+ITERS = 100
+SNR = 0.161
+BYTES_PER_EDGE = {"fp32": 16, "fp16": 12, "bf16": 12}   # per edge, frame and iteration
+PROFILE = os.path.join(ROOT, "profiles", "decode_kernel_rate0.1_Z12500_K128_T100.txt")
+KERNEL_SRC = os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", "decode.cu")
+
+
+def workload_name(msg: str) -> str:
+    return (f"rate-{RATE} QC-MET-LDPC [[A,0],[B,I70]] 72x80, Z={Z} (n=1e6), {K_FRAMES} codewords/GPU, "
+            f"SNR {SNR}, {ITERS} layered iterations, {msg.upper()} messages, no early termination")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("decode.cu", "qcmet_internal.h"):
+        with open(os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    with open(PROFILE) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline)
+
+def oracle_sample(code, cores: int, iters: int = 2):
+    """Time the FP64 oracle on `cores` frames x `iters` iterations; returns (Mbit/s, seconds, desc)."""
+    import oracle
+    fr = synth.make_frames(code, cores, SNR, first=10_000)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, iters, nthreads=cores)
+    dt = time.perf_counter() - t0
+    edge_updates = cores * iters * code.edges
+    rate = edge_updates / dt                                    # edge updates per second
+    mbit = code.n * rate / (code.edges * ITERS) / 1e6           # Mbit/s at 100 iterations
+    desc = (f"{cores} frames x {iters} iterations of the Z={code.Z} code ({edge_updates:.3g} edge "
+            f"updates, {dt:.1f} s wall on {cores} threads), scaled linearly to {ITERS} iterations")
+    return mbit, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    code = synth.make_code(RATE, Z)
+    cores = os.cpu_count() or 1
+    oracle_sample(code, 1, 1)   # untimed warm-up (build, page-in)
+    vals = []
+    desc = ""
+    for _ in range(max(args.steps, 1)):
+        v, dt, desc = oracle_sample(code, cores)
+        vals.append(v)
+    value = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mbit/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": K_FRAMES * code.n / (value * 1e6) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name("fp64 (oracle)"),
+                                        "parallelism": "host threads, one frame per thread"},
+        "cpu_baseline": {"value": value, "unit": "Mbit/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "Mbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2004_09084_gb300 as q
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else torch.cuda.current_device())
+    torch.cuda.set_device(dev)
+
+    code = synth.make_code(RATE, Z)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    fr = synth.make_frames(code, K_FRAMES, SNR, first=rank * K_FRAMES)
+    n = code.n
+    llr = torch.from_numpy(fr.llr).to(dev)
+    syn = torch.from_numpy(fr.syn).to(dev)
+    hard = torch.empty((K_FRAMES, n), dtype=torch.uint8, device=dev)
+    post = torch.empty((K_FRAMES, n), dtype=torch.float32, device=dev)
+    ok = torch.empty((K_FRAMES,), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        q.decode(qc, llr, syn, ITERS, hard=hard, llr_post=post, ok=ok, msg=args.msg,
+                 stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for _ in range(args.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+    ms = start.elapsed_time(end) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+
+    # decode quality of the last step (outside the timed region)
+    h_cpu = hard.cpu().numpy()
+    ok_cpu = ok.cpu().numpy()
+    fer = float(np.mean(np.any(h_cpu != fr.x, axis=1)))
+    ok_rate = float(np.mean(ok_cpu))
+
+    # end to end through the host-buffer entry point, pinned memory
+    pin_llr = torch.from_numpy(fr.llr).pin_memory()
+    pin_syn = torch.from_numpy(fr.syn).pin_memory()
+    pin_hard = torch.empty((K_FRAMES, n), dtype=torch.uint8).pin_memory()
+    pin_ok = torch.empty((K_FRAMES,), dtype=torch.uint8).pin_memory()
+    host_out = (pin_hard.numpy(), None, pin_ok.numpy())
+    q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
+                  stream=stream, out=host_out)
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
+                      stream=stream, out=host_out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = K_FRAMES * n * 4 + K_FRAMES * code.m
+    d2h = K_FRAMES * n + K_FRAMES
+
+    bits = world * K_FRAMES * n
+    value = bits / (ms * 1e-3) / 1e6
+    peak, peak_kind = peaks()
+    algo_bytes = BYTES_PER_EDGE[args.msg] * code.edges * K_FRAMES * ITERS
+    achieved = algo_bytes / (ms * 1e-3) / 1e9
+    info = qc.info()
+    # bytes the stateful part must move: messages and posteriors of the core
+    # columns, channel LLRs of the degree-1 columns (read once per iteration)
+    mbytes = 4 if args.msg == "fp32" else 2
+    core_edges = info["msg_slots"] * Z
+    deg1_edges = code.edges - core_edges
+    state_bytes = (core_edges * (8 + 2 * mbytes) + deg1_edges * 4) * K_FRAMES * ITERS
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v, dt, desc = oracle_sample(code, cores)
+        cpu = {"value": v, "unit": "Mbit/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mbit/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.msg == "fp32" else f"f32 ({args.msg} messages)",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args.msg), "K": K_FRAMES, "Z": Z, "n": n,
+                       "iterations": ITERS, "snr": SNR, "msg": args.msg,
+                       "parallelism": f"dp{world} (frames sharded, no collective)",
+                       "l2": "inputs larger than L2 (message state "
+                             f"{K_FRAMES * info['msg_slots'] * Z * mbytes / 1e9:.2f} GB per GPU)"},
+            "fer": fer, "ok_rate": ok_rate,
+            "e2e": {"value": bits / e2e_s / 1e6, "unit": "Mbit/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": profiled_traffic(),
+                         "peak_source": f"{peak_kind} hbm_gbs",
+                         "model": f"{BYTES_PER_EDGE[args.msg]} B per edge per frame per iteration",
+                         "stateful_bytes_frac": state_bytes / (ms * 1e-3) / 1e9 / peak},
+            "clocks": clocks,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile(args):
+    """Plain decode launches of a chosen size (no timing report); used under ncu."""
+    import torch
+
+    import paper_2004_09084_gb300 as q
+    code = synth.make_code(RATE, Z)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    fr = synth.make_frames(code, args.frames, SNR)
+    dev = torch.device("cuda", 0)
+    llr = torch.from_numpy(fr.llr).to(dev)
+    syn = torch.from_numpy(fr.syn).to(dev)
+    for _ in range(args.launches):
+        hard, post, ok = q.decode(qc, llr, syn, args.iters, msg=args.msg)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_case": {"frames": args.frames, "iters": args.iters,
+                                       "launches": args.launches, "msg": args.msg,
+                                       "ok_rate": float(ok.float().mean().item())}}))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--msg", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only run --launches decodes of --frames x --iters (for ncu captures)")
+    ap.add_argument("--frames", type=int, default=K_FRAMES)
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--launches", type=int, default=2)
+    args = ap.parse_args()
+    if args.profile:
+        return run_profile(args)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/*
+ * qcmet.h -- C ABI of the GB300 layered belief-propagation syndrome decoder for
+ * quasi-cyclic multi-edge-type (QC-MET) LDPC codes.
+ *
+ * Method: arXiv 2004.09084 (Li et al., "High-throughput GPU layered decoder of
+ * multi-edge type low density parity check codes in continuous-variable
+ * quantum key distribution systems"), Methods section, steps 1-4: layered
+ * sum-product decoding with the Phi check rule, where the syndrome bit s_m
+ * flips the sign of every message leaving check m.
+ *
+ * Conventions shared by every call:
+ *  - A code is a base matrix of mb x nb blocks and an expansion factor Z.  A
+ *    block with base[l*nb + c] = 1 is the Z x Z identity cyclically shifted to
+ *    the right by shifts[l*nb + c] (Results, the sentence after Eq. (m)), so
+ *    check l*Z + i is connected to variable c*Z + (i + shift) mod Z.  Blocks
+ *    with base = 0 are all-zero.  n = nb*Z variables, m = mb*Z checks.
+ *  - One decoding iteration visits every base row once ("layer", Methods).
+ *  - Frame-major layouts: frame k of an [K][n] array starts at element k*n.
+ *  - Status codes: QCMET_OK (0) or a negative QCMET_ERR_*; a failing call
+ *    never aborts or traps.  qcmet_last_error() returns a message for the
+ *    last failing call of the calling thread.
+ *
+ * Thread safety: distinct code handles are independent.  One handle owns
+ * device scratch; calls on the same handle must not run concurrently (on two
+ * host threads or on two streams that overlap on the GPU).
+ */
+#ifndef QCMET_H
+#define QCMET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QCMET_VERSION 100
+
+/* status codes */
+#define QCMET_OK 0
+#define QCMET_ERR_INVALID_ARG (-1)   /* null pointer, size out of range, bad enum     */
+#define QCMET_ERR_SHIFT_RANGE (-2)   /* a shift outside [0, Z) on a circulant block   */
+#define QCMET_ERR_DEGREE_LIMIT (-3)  /* a base row with more than QCMET_MAX_ROW_DEGREE */
+#define QCMET_ERR_ALIGNMENT (-4)     /* a device pointer not 16-byte aligned          */
+#define QCMET_ERR_OOM (-5)           /* device or host allocation failed              */
+#define QCMET_ERR_CUDA (-6)          /* a CUDA runtime call or a launch failed        */
+#define QCMET_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up            */
+#define QCMET_ERR_UNSUPPORTED (-8)   /* valid request this build does not serve       */
+
+/* Largest number of circulants in one base row (check degree in blocks). */
+#define QCMET_MAX_ROW_DEGREE 16
+
+/* Layer schedules (Results, Eqs. (m), (m1), (m2): merging unrelated rows).
+ *  NONE   -- one layer per base row, base-row order (the Methods schedule).
+ *  EXACT  -- rows that share no column with any row between them are merged;
+ *            the order of every pair of rows that share a column is kept, so
+ *            results are bit-identical to NONE.
+ *  GREEDY -- each row joins the first earlier layer it shares no column with
+ *            (the grouping of the paper's Eq. (m2) example); this may move a
+ *            row ahead of a related row and so changes the decoder's order. */
+#define QCMET_MERGE_NONE 0
+#define QCMET_MERGE_EXACT 1
+#define QCMET_MERGE_GREEDY 2
+
+/* Storage format of the check-to-variable messages L_rmn.  Arithmetic and the
+ * posteriors L_qn are FP32 in every format. */
+#define QCMET_MSG_FP32 0
+#define QCMET_MSG_FP16 1
+#define QCMET_MSG_BF16 2
+
+typedef struct qcmet_code qcmet_code; /* opaque, owned by the library */
+
+typedef struct {
+    int32_t mb, nb, Z;         /* base matrix shape and expansion factor          */
+    int32_t n, m;              /* variables nb*Z and checks mb*Z                   */
+    int64_t edges;             /* Tanner-graph edges: circulants * Z               */
+    int32_t circulants;        /* non-zero blocks                                  */
+    int32_t msg_slots;         /* circulants whose column has degree > 1           */
+    int32_t degree1_columns;   /* base columns of degree 1                         */
+    int32_t layers;            /* layers of the schedule after merging             */
+    int32_t max_row_degree;    /* largest number of circulants in one row          */
+    int32_t merge_mode;        /* QCMET_MERGE_*                                     */
+} qcmet_code_info;
+
+/*
+ * Build a code from its base matrix (Results, Eq. (m) and the H_compact
+ * description: which blocks are circulants, their shifts, Z).
+ *   base   : host [mb*nb] row-major, 1 = circulant, 0 = all-zero block
+ *   shifts : host [mb*nb] row-major, 0 <= shift < Z where base = 1, ignored elsewhere
+ *   merge_mode : QCMET_MERGE_* (qcmet_code_create uses QCMET_MERGE_EXACT)
+ *   out    : receives a handle; free it with qcmet_code_destroy
+ * The inputs are copied; the caller keeps ownership of its arrays.  Host-only:
+ * no GPU is touched until the first decode.  Errors: INVALID_ARG (null
+ * pointer, mb/nb/Z < 1, base value other than 0/1, n or m >= 2^31),
+ * SHIFT_RANGE, DEGREE_LIMIT, OOM.
+ */
+int qcmet_code_create(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb,
+                      int32_t Z, qcmet_code **out);
+int qcmet_code_create_ex(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb,
+                         int32_t Z, int32_t merge_mode, qcmet_code **out);
+
+/* Release a handle and every device buffer it owns.  Waits for the device to
+ * finish with them.  NULL is a no-op. */
+void qcmet_code_destroy(qcmet_code *code);
+
+/* Sizes of a code (host-only). */
+int qcmet_code_get_info(const qcmet_code *code, qcmet_code_info *info);
+
+/*
+ * The layer schedule (host-only): rows[0..mb) receives the base rows in the
+ * order one iteration visits them (rows with no circulant are left out and
+ * the remaining entries are -1); layer_first[0..layers] receives the index in
+ * rows[] where each layer starts.  Either pointer may be NULL.
+ */
+int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *layer_first);
+
+typedef struct {
+    int32_t msg_format;        /* QCMET_MSG_*; 0 = FP32                               */
+    int32_t threads_per_block; /* 0 = library default; else a multiple of 32, <= 1024 */
+    int32_t reserved[6];       /* set to 0                                          */
+} qcmet_decode_options;
+
+/*
+ * Decode K frames with a fixed number of layered iterations (Methods, steps
+ * 1-4; no early termination).
+ *   llr_ch   : device [K][n] FP32 channel LLRs 2R/sigma^2 (step 1)
+ *   syndrome : device [K][m] uint8, s_m in {0,1} (step 2); only bit 0 is read
+ *   K        : frames, >= 0 (0 is a no-op)
+ *   iterations : >= 0; 0 returns the hard decision of the channel LLRs
+ *   hard     : device [K][n] uint8 out, c_n = 1 iff L_qn < 0 (step 4)
+ *   llr_post : device [K][n] FP32 out, the posteriors L_qn after the last
+ *              layer of the last iteration; may be NULL
+ *   ok       : device [K] uint8 out, 1 iff H*hard = syndrome for that frame
+ *   stream   : cudaStream_t (NULL = legacy default stream); the call only
+ *              enqueues work and returns (stream-ordered, asynchronous)
+ * Every device pointer must be 16-byte aligned (ALIGNMENT otherwise) and
+ * must not overlap another.  The library keeps per-handle device scratch for
+ * the messages (K * msg_slots * Z values), grown on demand, and uploads the
+ * code's layer table on the first call.  Errors: INVALID_ARG, ALIGNMENT, OOM,
+ * CUDA, UNSUPPORTED.
+ */
+int qcmet_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                 int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
+                 void *stream);
+
+/* qcmet_decode with options (NULL = defaults). */
+int qcmet_decode_ex(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                    int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
+                    const qcmet_decode_options *opts, void *stream);
+
+/*
+ * qcmet_decode_ex for callers whose data live in host memory: every pointer
+ * is a host pointer (pinned memory gives the fastest copies).  The call
+ * copies the inputs to library-owned device buffers on `stream`, decodes,
+ * copies hard / llr_post (if not NULL) / ok back, and synchronises `stream`
+ * before it returns.
+ */
+int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                      int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
+                      const qcmet_decode_options *opts, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *qcmet_last_error(void);
+
+/* Fixed description of a status code. */
+const char *qcmet_status_string(int status);
+
+/* QCMET_VERSION of the loaded library. */
+int qcmet_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QCMET_H */

@@ -1,0 +1,305 @@
+// C ABI of the decoder library: argument checks, per-handle device state and
+// the calls declared in include/qcmet.h.  The decode itself is one launch of
+// the fused kernel in decode.cu.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "qcmet_internal.h"
+
+struct qcmet_code {
+    qcmet::Code c;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const std::string &msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(const char *what, cudaError_t e) {
+    return fail(e == cudaErrorMemoryAllocation ? QCMET_ERR_OOM : QCMET_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 4 : 2; }
+
+// Upload the schedule image once, on the current device.
+int ensure_device(qcmet::Code &c) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    if (c.d_image) {
+        if (dev != c.device)
+            return fail(QCMET_ERR_UNSUPPORTED, "code handle was first used on device " +
+                                                   std::to_string(c.device) +
+                                                   "; create one handle per device");
+        return QCMET_OK;
+    }
+    const size_t bytes = c.image.words.size() * sizeof(int32_t);
+    void *p = nullptr;
+    e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail("cudaMalloc(schedule)", e);
+    e = cudaMemcpy(p, c.image.words.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return cuda_fail("cudaMemcpy(schedule)", e);
+    }
+    c.d_image = static_cast<int32_t *>(p);
+    c.image_bytes = bytes;
+    c.device = dev;
+    return QCMET_OK;
+}
+
+// Grow a device buffer to at least `need` bytes (contents are not kept).
+int grow(void **buf, size_t *have, size_t need, const char *what) {
+    if (*have >= need) return QCMET_OK;
+    if (*buf) {
+        cudaError_t e = cudaFree(*buf);
+        if (e != cudaSuccess) return cuda_fail("cudaFree", e);
+        *buf = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        return cuda_fail(what, e);
+    }
+    *have = need;
+    return QCMET_OK;
+}
+
+int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads) {
+    *fmt = QCMET_MSG_FP32;
+    *threads = 0;
+    if (!o) return QCMET_OK;
+    if (o->msg_format != QCMET_MSG_FP32 && o->msg_format != QCMET_MSG_FP16 &&
+        o->msg_format != QCMET_MSG_BF16)
+        return fail(QCMET_ERR_INVALID_ARG, "unknown msg_format");
+    if (o->threads_per_block != 0 &&
+        (o->threads_per_block < 32 || o->threads_per_block > 1024 || o->threads_per_block % 32))
+        return fail(QCMET_ERR_INVALID_ARG, "threads_per_block must be 0 or a multiple of 32 in [32, 1024]");
+    for (int32_t r : o->reserved)
+        if (r != 0) return fail(QCMET_ERR_INVALID_ARG, "reserved option fields must be 0");
+    *fmt = o->msg_format;
+    *threads = o->threads_per_block;
+    return QCMET_OK;
+}
+
+int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
+                  int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok,
+                  const qcmet_decode_options *opts, void *stream) {
+    int32_t fmt, threads;
+    int st = check_options(opts, &fmt, &threads);
+    if (st) return st;
+    if (K < 0) return fail(QCMET_ERR_INVALID_ARG, "K must be >= 0");
+    if (T < 0) return fail(QCMET_ERR_INVALID_ARG, "iterations must be >= 0");
+    if (K == 0) return QCMET_OK;
+    if (!llr_ch || !syndrome || !hard || !ok)
+        return fail(QCMET_ERR_INVALID_ARG, "llr_ch, syndrome, hard and ok must not be NULL");
+    if (!aligned16(llr_ch) || !aligned16(syndrome) || !aligned16(hard) || !aligned16(ok) ||
+        (llr_post && !aligned16(llr_post)))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    st = ensure_device(c);
+    if (st) return st;
+
+    const size_t n = (size_t)c.nb * c.Z;
+    const size_t stride = qcmet::slot_stride(c.Z);
+    const size_t need_msgs = (size_t)K * (size_t)c.msg_slots * stride * msg_bytes(fmt);
+    st = grow(&c.d_msgs, &c.msgs_bytes, need_msgs ? need_msgs : 16, "cudaMalloc(messages)");
+    if (st) return st;
+    float *post = llr_post;
+    if (!post) {
+        void *p = c.d_post;
+        st = grow(&p, &c.post_bytes, (size_t)K * n * sizeof(float), "cudaMalloc(posteriors)");
+        c.d_post = static_cast<float *>(p);
+        if (st) return st;
+        post = c.d_post;
+    }
+
+    qcmet::DecodeArgs a;
+    a.ch = llr_ch;
+    a.syn = syndrome;
+    a.post = post;
+    a.msgs = c.d_msgs;
+    a.hard = hard;
+    a.ok = ok;
+    a.image = c.d_image;
+    a.image_words = (int32_t)c.image.words.size();
+    a.K = K;
+    a.T = T;
+    a.Z = c.Z;
+    a.n = (int32_t)n;
+    a.m = c.mb * c.Z;
+    a.nb = c.nb;
+    a.msg_slots = c.msg_slots;
+    a.slot_stride = (int64_t)stride;
+    std::string err;
+    st = qcmet::launch_decode(a, fmt, threads, stream, err);
+    if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" {
+
+int qcmet_code_create_ex(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb,
+                         int32_t Z, int32_t merge_mode, qcmet_code **out) {
+    if (!out) return fail(QCMET_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    qcmet_code *h = new (std::nothrow) qcmet_code;
+    if (!h) return fail(QCMET_ERR_OOM, "host allocation failed");
+    std::string err;
+    int st;
+    try {
+        st = qcmet::build_code(base, shifts, mb, nb, Z, merge_mode, h->c, err);
+    } catch (const std::bad_alloc &) {
+        st = QCMET_ERR_OOM;
+        err = "host allocation failed";
+    }
+    if (st) {
+        delete h;
+        return fail(st, err);
+    }
+    *out = h;
+    return QCMET_OK;
+}
+
+int qcmet_code_create(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb,
+                      int32_t Z, qcmet_code **out) {
+    return qcmet_code_create_ex(base, shifts, mb, nb, Z, QCMET_MERGE_EXACT, out);
+}
+
+void qcmet_code_destroy(qcmet_code *code) {
+    if (!code) return;
+    qcmet::Code &c = code->c;
+    if (c.d_image) cudaFree(c.d_image);
+    if (c.d_msgs) cudaFree(c.d_msgs);
+    if (c.d_post) cudaFree(c.d_post);
+    if (c.d_io) cudaFree(c.d_io);
+    delete code;
+}
+
+int qcmet_code_get_info(const qcmet_code *code, qcmet_code_info *info) {
+    if (!code || !info) return fail(QCMET_ERR_INVALID_ARG, "code and info must not be NULL");
+    const qcmet::Code &c = code->c;
+    info->mb = c.mb;
+    info->nb = c.nb;
+    info->Z = c.Z;
+    info->n = c.nb * c.Z;
+    info->m = c.mb * c.Z;
+    info->edges = (int64_t)c.circulants * c.Z;
+    info->circulants = c.circulants;
+    info->msg_slots = c.msg_slots;
+    info->degree1_columns = c.degree1_columns;
+    info->layers = (int32_t)c.layer_first.size() - 1;
+    info->max_row_degree = c.max_row_degree;
+    info->merge_mode = c.merge_mode;
+    return QCMET_OK;
+}
+
+int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *layer_first) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    const qcmet::Code &c = code->c;
+    if (rows) {
+        for (int32_t i = 0; i < c.mb; ++i)
+            rows[i] = i < (int32_t)c.sched_rows.size() ? c.sched_rows[i] : -1;
+    }
+    if (layer_first)
+        std::memcpy(layer_first, c.layer_first.data(), c.layer_first.size() * sizeof(int32_t));
+    return QCMET_OK;
+}
+
+int qcmet_decode_ex(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                    int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
+                    const qcmet_decode_options *opts, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    return decode_device(const_cast<qcmet_code *>(code)->c, llr_ch, syndrome, K, iterations, hard,
+                         llr_post, ok, opts, stream);
+}
+
+int qcmet_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome, int32_t K,
+                 int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok, void *stream) {
+    return qcmet_decode_ex(code, llr_ch, syndrome, K, iterations, hard, llr_post, ok, nullptr,
+                           stream);
+}
+
+int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                      int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
+                      const qcmet_decode_options *opts, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    if (K < 0) return fail(QCMET_ERR_INVALID_ARG, "K must be >= 0");
+    if (iterations < 0) return fail(QCMET_ERR_INVALID_ARG, "iterations must be >= 0");
+    if (K == 0) return QCMET_OK;
+    if (!llr_ch || !syndrome || !hard || !ok)
+        return fail(QCMET_ERR_INVALID_ARG, "llr_ch, syndrome, hard and ok must not be NULL");
+    qcmet::Code &c = const_cast<qcmet_code *>(code)->c;
+    int st = ensure_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
+    const size_t b_ch = round256((size_t)K * n * sizeof(float));
+    const size_t b_syn = round256((size_t)K * m);
+    const size_t b_hard = round256((size_t)K * n);
+    const size_t b_post = llr_post ? round256((size_t)K * n * sizeof(float)) : 0;
+    const size_t b_ok = round256((size_t)K);
+    st = grow(&c.d_io, &c.io_bytes, b_ch + b_syn + b_hard + b_post + b_ok, "cudaMalloc(staging)");
+    if (st) return st;
+    char *base = static_cast<char *>(c.d_io);
+    float *d_ch = reinterpret_cast<float *>(base);
+    uint8_t *d_syn = reinterpret_cast<uint8_t *>(base + b_ch);
+    uint8_t *d_hard = reinterpret_cast<uint8_t *>(base + b_ch + b_syn);
+    float *d_post = llr_post ? reinterpret_cast<float *>(base + b_ch + b_syn + b_hard) : nullptr;
+    uint8_t *d_ok = reinterpret_cast<uint8_t *>(base + b_ch + b_syn + b_hard + b_post);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(d_ch, llr_ch, (size_t)K * n * sizeof(float),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(llr_ch)", e);
+    e = cudaMemcpyAsync(d_syn, syndrome, (size_t)K * m, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(syndrome)", e);
+    st = decode_device(c, d_ch, d_syn, K, iterations, d_hard, d_post, d_ok, opts, stream);
+    if (st) return st;
+    e = cudaMemcpyAsync(hard, d_hard, (size_t)K * n, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(hard)", e);
+    if (llr_post) {
+        e = cudaMemcpyAsync(llr_post, d_post, (size_t)K * n * sizeof(float),
+                            cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(llr_post)", e);
+    }
+    e = cudaMemcpyAsync(ok, d_ok, (size_t)K, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(ok)", e);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail("cudaStreamSynchronize", e);
+    return QCMET_OK;
+}
+
+const char *qcmet_last_error(void) { return g_last_error.c_str(); }
+
+const char *qcmet_status_string(int status) {
+    switch (status) {
+        case QCMET_OK: return "ok";
+        case QCMET_ERR_INVALID_ARG: return "invalid argument";
+        case QCMET_ERR_SHIFT_RANGE: return "circulant shift outside [0, Z)";
+        case QCMET_ERR_DEGREE_LIMIT: return "row degree above QCMET_MAX_ROW_DEGREE";
+        case QCMET_ERR_ALIGNMENT: return "pointer not 16-byte aligned";
+        case QCMET_ERR_OOM: return "out of memory";
+        case QCMET_ERR_CUDA: return "CUDA error";
+        case QCMET_ERR_TIMEOUT: return "device wait timed out";
+        case QCMET_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int qcmet_version(void) { return QCMET_VERSION; }
+
+}  // extern "C"

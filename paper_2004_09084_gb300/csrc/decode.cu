@@ -1,0 +1,512 @@
+// Fused layered belief-propagation decoder for QC-MET-LDPC syndrome decoding
+// on GB300 (sm_103a).
+//
+// Method (arXiv 2004.09084, Methods, steps 1-4): for every iteration and every
+// layer (base row) l, each check m of the layer forms the variable-to-check
+// messages q = L_qn - L_rmn(old) (step 3, first equation), computes the new
+// check-to-variable messages with the sum-product rule and the syndrome sign
+// (step 2), and writes L_qn = q + L_rmn(new) (step 3, second equation).  The
+// hard decision c_n = [L_qn < 0] closes the decode (step 4).
+//
+// GB300 design (ours, not the paper's):
+//  * Frames are independent, so one CTA owns one frame for the whole decode
+//    and a layer boundary costs one block barrier.  The whole decode -- init,
+//    T x layers, hard decision, syndrome test -- is a single launch.
+//  * Frame-major state: posteriors L_qn [K][n] live in the caller's llr_post
+//    buffer (FP32), messages [K][slot][Z] in FP32 / FP16 / BF16.  Within a
+//    circulant, consecutive checks touch consecutive variables, so a warp's
+//    gathers are contiguous runs of 128 B (one wrap at most).
+//  * Degree-1 variables (a base column with a single circulant) keep no state:
+//    for them L_qn - L_rmn(old) equals the channel LLR exactly, so q is read
+//    from the channel array and L_qn is written once, in the last iteration.
+//  * While a row is processed, warp 0 issues bulk L2 prefetches of the next
+//    row's message slots, posterior columns, channel columns and syndrome
+//    bits, so HBM streams ahead of the layer barrier.
+//  * The check rule is evaluated in the tanh-product form
+//    |r_e| = 2 atanh(prod_{k != e} tanh(|q_k|/2)), which equals
+//    Phi(sum_{k != e} Phi(|q_k|)) (Methods, step 2).  With u_k = exp(-|q_k|),
+//    prod (1 + u_k J) over the other edges (J the 2x2 swap) is alpha I + beta J
+//    with alpha, beta the even and odd elementary symmetric sums of the u_k,
+//    and |r_e| = ln(alpha / beta).  Every term is positive, so there is no
+//    cancellation at either end of the LLR range; the exclusive products come
+//    from prefix and suffix products (no division).
+//  * Clipping: |q| is clipped to 30 before the rule and |r| to
+//    [Phi(30), 30] after it -- the same function as clipping both Phi
+//    arguments to [Phi(30), 30].
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "qcmet_internal.h"
+
+namespace qcmet {
+
+namespace {
+
+constexpr float kClipMax = 30.0f;
+// Phi(30) = 2 atanh(exp(-30)), the lower end of the clipping interval.
+constexpr float kClipMin = 1.8715246e-13f;
+constexpr float kLn2 = 0.693147180559945309f;
+constexpr float kLog2e = 1.442695040888963407f;
+constexpr int kDefaultThreads = 1024;
+
+// ---- message storage formats ---------------------------------------------
+
+template <typename M>
+struct Msg;
+
+template <>
+struct Msg<float> {
+    static __device__ __forceinline__ float load(const float *p) { return *p; }
+    static __device__ __forceinline__ float quantize(float x) { return x; }
+    static __device__ __forceinline__ void store(float *p, float x) { *p = x; }
+};
+
+template <>
+struct Msg<__half> {
+    static __device__ __forceinline__ float load(const __half *p) { return __half2float(*p); }
+    static __device__ __forceinline__ float quantize(float x) {
+        return __half2float(__float2half_rn(x));
+    }
+    static __device__ __forceinline__ void store(__half *p, float x) { *p = __float2half_rn(x); }
+};
+
+template <>
+struct Msg<__nv_bfloat16> {
+    static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
+        return __bfloat162float(*p);
+    }
+    static __device__ __forceinline__ float quantize(float x) {
+        return __bfloat162float(__float2bfloat16_rn(x));
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float x) {
+        *p = __float2bfloat16_rn(x);
+    }
+};
+
+// ---- L2 prefetch -----------------------------------------------------------
+
+// Prefetch bytes [off, off + len) of a buffer that starts 16-byte aligned and
+// holds `total` bytes.  The range is widened to 16-byte boundaries and clipped
+// to the buffer, as cp.async.bulk requires aligned addresses and sizes.
+__device__ __forceinline__ void prefetch_l2(const void *buf, size_t total, size_t off, size_t len) {
+    size_t lo = off & ~size_t(15);
+    size_t hi = (off + len + 15) & ~size_t(15);
+    const size_t cap = total & ~size_t(15);
+    if (hi > cap) hi = cap;
+    const char *p = static_cast<const char *>(buf);
+    while (lo < hi) {
+        const size_t chunk = (hi - lo) > 32768 ? 32768 : (hi - lo);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + lo),
+                     "r"(static_cast<unsigned>(chunk))
+                     : "memory");
+        lo += chunk;
+    }
+}
+
+// ---- shared-memory view of the schedule ------------------------------------
+
+struct Sched {
+    const int32_t *w;
+    int32_t n_rows, n_layers, nb, Z, mb, n_zero_rows;
+    const int32_t *layer_first;
+    const int4 *rows;     // DevRow
+    const int4 *entries;  // DevEntry
+    const int32_t *col_kind;
+    const int32_t *zero_rows;
+};
+
+__device__ __forceinline__ Sched make_sched(const int32_t *w) {
+    Sched s;
+    s.w = w;
+    s.n_rows = w[kHdrRows];
+    s.n_layers = w[kHdrLayers];
+    s.nb = w[kHdrNb];
+    s.Z = w[kHdrZ];
+    s.mb = w[kHdrMb];
+    s.n_zero_rows = w[kHdrZeroRows];
+    s.layer_first = w + w[kHdrOffLayerFirst];
+    s.rows = reinterpret_cast<const int4 *>(w + w[kHdrOffRows]);
+    s.entries = reinterpret_cast<const int4 *>(w + w[kHdrOffEntries]);
+    s.col_kind = w + w[kHdrOffColKind];
+    s.zero_rows = w + w[kHdrOffZeroRows];
+    return s;
+}
+
+// Per-frame views of the global arrays.
+template <typename M>
+struct Frame {
+    const float *ch;     // [n]
+    const uint8_t *syn;  // [m]
+    float *post;         // [n]
+    M *msg;              // [slots][stride]
+};
+
+// ---- one check node ----------------------------------------------------------
+
+// (a, b) (x) (c, d): product of two elements a I + b J and c I + d J.
+__device__ __forceinline__ void cmul(float a, float b, float c, float d, float &x, float &y) {
+    x = fmaf(a, c, b * d);
+    y = fmaf(a, d, b * c);
+}
+
+// For local edges e = 0..E-1 with u[e] = exp(-|q_e|), call
+// emit(e, alpha_e, beta_e) where alpha_e I + beta_e J is
+// (oa I + ob J) * prod_{k != e} (I + u_k J).
+template <int E, typename Emit>
+__device__ __forceinline__ void exclusive_products(const float (&u)[E], float oa, float ob,
+                                                   Emit &&emit) {
+    if constexpr (E <= 6) {
+        float pa[E], pb[E];
+        pa[0] = oa;
+        pb[0] = ob;
+#pragma unroll
+        for (int e = 1; e < E; ++e) {
+            pa[e] = fmaf(u[e - 1], pb[e - 1], pa[e - 1]);
+            pb[e] = fmaf(u[e - 1], pa[e - 1], pb[e - 1]);
+        }
+        float sa = 1.0f, sb = 0.0f;
+#pragma unroll
+        for (int e = E - 1; e >= 0; --e) {
+            float a, b;
+            cmul(pa[e], pb[e], sa, sb, a, b);
+            const float nsa = fmaf(u[e], sb, sa);
+            const float nsb = fmaf(u[e], sa, sb);
+            sa = nsa;
+            sb = nsb;
+            emit(e, a, b);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            float a = oa, b = ob;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                if (k == e) continue;
+                const float na = fmaf(u[k], b, a);
+                const float nb = fmaf(u[k], a, b);
+                a = na;
+                b = nb;
+            }
+            emit(e, a, b);
+        }
+    }
+}
+
+// Gather the V2C message q = L_qn - L_rmn(old) of edge `en` at check i.
+template <typename M>
+__device__ __forceinline__ float gather_q(const int4 &en, int i, const Frame<M> &fr, int Z,
+                                          size_t stride, bool first) {
+    int j = i + en.y;
+    j = j >= Z ? j - Z : j;
+    const int v = en.x + j;
+    if (en.z < 0) return fr.ch[v];  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
+    const float lv = fr.post[v];
+    const float ro = first ? 0.0f : Msg<M>::load(fr.msg + (size_t)en.z * stride + i);
+    return lv - ro;
+}
+
+// Write the new C2V message of edge `en` and the posterior L_qn = q + r.
+template <typename M>
+__device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float a, float b,
+                                          unsigned par, const Frame<M> &fr, int Z, size_t stride,
+                                          bool last) {
+    if (en.z < 0 && !last) return;
+    float mag = kLn2 * (__log2f(a) - __log2f(b));
+    mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+    const bool neg = ((par ^ (q < 0.0f ? 1u : 0u)) & 1u) != 0u;
+    float rn = neg ? -mag : mag;
+    int j = i + en.y;
+    j = j >= Z ? j - Z : j;
+    const int v = en.x + j;
+    if (en.z >= 0) {
+        rn = Msg<M>::quantize(rn);
+        Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
+    }
+    fr.post[v] = q + rn;
+}
+
+__device__ __forceinline__ float u_of(float q) {
+    return exp2f(-kLog2e * fminf(fabsf(q), kClipMax));
+}
+
+// Rows of degree D <= 8: one thread per check.
+//   first: iteration 0 (old messages are zero and are not read)
+//   last : final iteration (degree-1 variables get their posterior)
+template <int D, typename M>
+__device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_base,
+                                        const Frame<M> &fr, int Z, size_t stride, bool first,
+                                        bool last) {
+    for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+        float q[D], u[D];
+        unsigned par = fr.syn[check_base + i] & 1u;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            q[e] = gather_q<M>(ent[e], i, fr, Z, stride, first);
+            par ^= q[e] < 0.0f ? 1u : 0u;
+            u[e] = u_of(q[e]);
+        }
+        exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+            scatter_r<M>(ent[e], i, q[e], a, b, par, fr, Z, stride, last);
+        });
+    }
+}
+
+// Rows of degree 9..16: two lanes per check (lanes l and l ^ 16 of a warp).
+// Each lane owns E = ceil(D/2) edges; the lanes swap their partial products
+// and sign parities with one shuffle each.
+template <int D, typename M>
+__device__ __forceinline__ void run_row_pair(const int4 *__restrict__ ent, int check_base,
+                                             const Frame<M> &fr, int Z, size_t stride, bool first,
+                                             bool last) {
+    constexpr int E = (D + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int part = lane >> 4;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int i0 = warp * 16; i0 < Z; i0 += nwarps * 16) {
+        const int i = i0 + (lane & 15);
+        const bool valid = i < Z;
+        float q[E], u[E];
+        unsigned par = (valid && part == 0) ? (fr.syn[check_base + i] & 1u) : 0u;
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const int e = part * E + el;
+            if (valid && e < D) {
+                q[el] = gather_q<M>(ent[e], i, fr, Z, stride, first);
+                par ^= q[el] < 0.0f ? 1u : 0u;
+                u[el] = u_of(q[el]);
+            } else {
+                q[el] = 0.0f;
+                u[el] = 0.0f;  // the identity factor I + 0 J
+            }
+        }
+        // product over this lane's edges
+        float ta = 1.0f, tb = 0.0f;
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const float na = fmaf(u[el], tb, ta);
+            const float nb = fmaf(u[el], ta, tb);
+            ta = na;
+            tb = nb;
+        }
+        const float oa = __shfl_xor_sync(0xffffffffu, ta, 16);
+        const float ob = __shfl_xor_sync(0xffffffffu, tb, 16);
+        par ^= __shfl_xor_sync(0xffffffffu, par, 16);
+        if (!valid) continue;
+        exclusive_products<E>(u, oa, ob, [&](int el, float a, float b) {
+            const int e = part * E + el;
+            if (e < D) scatter_r<M>(ent[e], i, q[el], a, b, par, fr, Z, stride, last);
+        });
+    }
+}
+
+template <typename M>
+__device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int check_base,
+                                             const Frame<M> &fr, int Z, size_t stride, bool first,
+                                             bool last) {
+    switch (degree) {
+#define QCMET_ROW_CASE(DD) \
+    case DD: run_row<DD, M>(ent, check_base, fr, Z, stride, first, last); break;
+#define QCMET_PAIR_CASE(DD) \
+    case DD: run_row_pair<DD, M>(ent, check_base, fr, Z, stride, first, last); break;
+        QCMET_ROW_CASE(1)
+        QCMET_ROW_CASE(2)
+        QCMET_ROW_CASE(3)
+        QCMET_ROW_CASE(4)
+        QCMET_ROW_CASE(5)
+        QCMET_ROW_CASE(6)
+        QCMET_ROW_CASE(7)
+        QCMET_ROW_CASE(8)
+        QCMET_PAIR_CASE(9)
+        QCMET_PAIR_CASE(10)
+        QCMET_PAIR_CASE(11)
+        QCMET_PAIR_CASE(12)
+        QCMET_PAIR_CASE(13)
+        QCMET_PAIR_CASE(14)
+        QCMET_PAIR_CASE(15)
+        QCMET_PAIR_CASE(16)
+#undef QCMET_ROW_CASE
+#undef QCMET_PAIR_CASE
+        default: break;
+    }
+}
+
+// Warp 0 prefetches into L2 what scheduled row `j` of iteration `t` will read.
+template <typename M>
+__device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a, int f, int j,
+                                             int t) {
+    const int lane = threadIdx.x;  // only warp 0 calls this
+    const int4 row = s.rows[j];
+    const size_t Z = (size_t)s.Z;
+    const size_t n = (size_t)a.n;
+    const size_t fl_bytes = (size_t)a.K * n * sizeof(float);
+    if (lane < row.y) {
+        const int4 en = s.entries[row.x + lane];
+        const size_t col_off = ((size_t)f * n + (size_t)en.x) * sizeof(float);
+        if (en.z >= 0) {
+            if (t > 0) {
+                const M *slot = static_cast<const M *>(a.msgs) +
+                                ((size_t)f * a.msg_slots + (size_t)en.z) * (size_t)a.slot_stride;
+                // the slot stride is a multiple of 16 elements: the widened range stays inside it
+                prefetch_l2(slot, ((Z * sizeof(M)) + 15) & ~size_t(15), 0, Z * sizeof(M));
+            }
+            prefetch_l2(a.post, fl_bytes, col_off, Z * sizeof(float));
+        } else {
+            prefetch_l2(a.ch, fl_bytes, col_off, Z * sizeof(float));
+        }
+    } else if (lane == 31) {
+        prefetch_l2(a.syn, (size_t)a.K * (size_t)a.m, (size_t)f * a.m + (size_t)row.z, Z);
+    }
+}
+
+template <typename M>
+__global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a) {
+    extern __shared__ int4 smem_i4[];
+    int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(a.image);
+        for (int k = threadIdx.x; k < a.image_words / 4; k += blockDim.x) smem_i4[k] = src[k];
+    }
+    __syncthreads();
+    const Sched s = make_sched(sw);
+    const int Z = s.Z;
+    const size_t n = (size_t)a.n;
+    const size_t stride = (size_t)a.slot_stride;
+    const int T = a.T;
+
+    for (int f = blockIdx.x; f < a.K; f += gridDim.x) {
+        Frame<M> fr;
+        fr.ch = a.ch + (size_t)f * n;
+        fr.syn = a.syn + (size_t)f * (size_t)a.m;
+        fr.post = a.post + (size_t)f * n;
+        fr.msg = static_cast<M *>(a.msgs) + (size_t)f * (size_t)a.msg_slots * stride;
+
+        // Step 1: L_qn = channel LLR for every variable that carries state.
+        for (int c = 0; c < s.nb; ++c) {
+            if (s.col_kind[c] != kColCore) continue;
+            const float *src = fr.ch + (size_t)c * Z;
+            float *dst = fr.post + (size_t)c * Z;
+            for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
+        }
+        if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
+        __syncthreads();
+
+        // Steps 2-3 over T iterations x layers.
+        for (int t = 0; t < T; ++t) {
+            const bool first = t == 0;
+            const bool last = t == T - 1;
+            for (int layer = 0; layer < s.n_layers; ++layer) {
+                for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
+                    if (threadIdx.x < 32) {
+                        if (j + 1 < s.n_rows) prefetch_row<M>(s, a, f, j + 1, t);
+                        else if (!last) prefetch_row<M>(s, a, f, 0, t + 1);
+                    }
+                    const int4 row = s.rows[j];
+                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, last);
+                }
+                __syncthreads();
+            }
+        }
+
+        // Step 4: posteriors of stateless columns, hard decisions.
+        for (int c = 0; c < s.nb; ++c) {
+            const int kind = s.col_kind[c];
+            const bool from_channel = kind == kColUnconnected || (kind == kColDegree1 && T == 0);
+            const size_t base = (size_t)c * Z;
+            for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+                float L;
+                if (from_channel) {
+                    L = fr.ch[base + i];
+                    fr.post[base + i] = L;
+                } else {
+                    L = fr.post[base + i];
+                }
+                a.hard[(size_t)f * n + base + i] = L < 0.0f ? 1 : 0;
+            }
+        }
+        __syncthreads();
+
+        // Syndrome test: ok = [H c = s].
+        const uint8_t *hard = a.hard + (size_t)f * n;
+        int fail = 0;
+        for (int j = 0; j < s.n_rows; ++j) {
+            const int4 row = s.rows[j];
+            const int4 *ent = s.entries + row.x;
+            for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+                unsigned par = fr.syn[row.z + i] & 1u;
+                for (int e = 0; e < row.y; ++e) {
+                    const int4 en = ent[e];
+                    int jj = i + en.y;
+                    jj = jj >= Z ? jj - Z : jj;
+                    par ^= hard[en.x + jj];
+                }
+                fail |= (int)par;
+            }
+        }
+        for (int zr = 0; zr < s.n_zero_rows; ++zr) {
+            const size_t cb = (size_t)s.zero_rows[zr] * Z;
+            for (int i = threadIdx.x; i < Z; i += blockDim.x) fail |= fr.syn[cb + i] & 1;
+        }
+        fail = __syncthreads_or(fail);
+        if (threadIdx.x == 0) a.ok[f] = fail ? 0 : 1;
+        __syncthreads();
+    }
+}
+
+int sm_count_cached() {
+    static int count[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev < 0 || dev >= 64) return 0;
+    if (!count[dev]) cudaDeviceGetAttribute(&count[dev], cudaDevAttrMultiProcessorCount, dev);
+    return count[dev];
+}
+
+template <typename M>
+int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &err) {
+    const size_t smem = (size_t)a.image_words * sizeof(int32_t);
+    auto kern = decode_kernel<M>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return QCMET_ERR_UNSUPPORTED;
+        }
+    }
+    const int sms = sm_count_cached();
+    if (sms <= 0) {
+        err = "no CUDA device";
+        return QCMET_ERR_CUDA;
+    }
+    const int grid = a.K < sms ? a.K : sms;
+    kern<<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("decode launch: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    return QCMET_OK;
+}
+
+}  // namespace
+
+int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
+                  std::string &err) {
+    if (threads == 0) threads = kDefaultThreads;
+    if (threads < 32 || threads > kDefaultThreads || threads % 32) {
+        err = "threads_per_block must be a multiple of 32 in [32, 1024]";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    switch (msg_format) {
+        case QCMET_MSG_FP32: return launch_typed<float>(a, threads, stream, err);
+        case QCMET_MSG_FP16: return launch_typed<__half>(a, threads, stream, err);
+        case QCMET_MSG_BF16: return launch_typed<__nv_bfloat16>(a, threads, stream, err);
+        default: err = "unknown message format"; return QCMET_ERR_INVALID_ARG;
+    }
+}
+
+}  // namespace qcmet

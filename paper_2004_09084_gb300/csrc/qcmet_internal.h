@@ -1,0 +1,116 @@
+// Internal declarations shared by the host builder, the C ABI glue and the
+// CUDA kernels of the decoder library.  Not installed; not part of the ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/qcmet.h"
+
+namespace qcmet {
+
+// Column classes of the base matrix.
+enum ColumnKind : int32_t {
+    kColUnconnected = 0,  // no circulant in the column: L_qn stays the channel LLR
+    kColDegree1 = 1,      // one circulant: L_qn - L_rmn(old) is the channel LLR exactly
+    kColCore = 2,         // two or more circulants: posterior and messages are state
+};
+
+// One circulant of a base row as the layer kernel reads it.
+struct DevEntry {
+    int32_t var_base;  // c * Z: first variable of the block column
+    int32_t shift;     // circulant shift a
+    int32_t slot;      // message slot for core columns, -1 for a degree-1 column
+    int32_t col;       // base column c
+};
+
+// One scheduled base row.
+struct DevRow {
+    int32_t first_entry;  // index of its first DevEntry
+    int32_t degree;       // number of circulants (1..QCMET_MAX_ROW_DEGREE)
+    int32_t check_base;   // l * Z: first check of the row
+    int32_t row;          // base row l
+};
+
+// Flat device image of a code's schedule: a header followed by int32 arrays.
+// Layout (all int32, offsets in elements from the start):
+//   header[kHdrWords]: see the kHdr* indices below
+//   layer_first[n_layers + 1]           (padded to a multiple of 4)
+//   rows[n_rows]   (DevRow, 4 ints each)
+//   entries[n_entries] (DevEntry, 4 ints each)
+//   col_kind[nb]                         (padded to a multiple of 4)
+//   zero_rows[...]: base rows with no circulant (their checks test s_m = 0)
+enum : int32_t {
+    kHdrRows = 0, kHdrLayers, kHdrEntries, kHdrNb, kHdrZ, kHdrMb,
+    kHdrOffLayerFirst, kHdrOffRows, kHdrOffEntries, kHdrOffColKind, kHdrOffZeroRows,
+    kHdrZeroRows, kHdrWords
+};
+
+struct ScheduleImage {
+    std::vector<int32_t> words;
+    int32_t off_layer_first = 0;
+    int32_t off_rows = 0;
+    int32_t off_entries = 0;
+    int32_t off_col_kind = 0;
+    int32_t off_zero_rows = 0;
+    int32_t n_zero_rows = 0;
+};
+
+struct Code {
+    int32_t mb = 0, nb = 0, Z = 0;
+    int32_t merge_mode = QCMET_MERGE_EXACT;
+    std::vector<int8_t> base;
+    std::vector<int32_t> shifts;
+    std::vector<int32_t> col_degree;        // [nb]
+    std::vector<int32_t> sched_rows;        // base rows in visiting order
+    std::vector<int32_t> layer_first;       // [layers + 1] into sched_rows
+    std::vector<int32_t> zero_rows;         // rows with no circulant
+    int32_t circulants = 0;
+    int32_t msg_slots = 0;
+    int32_t degree1_columns = 0;
+    int32_t max_row_degree = 0;
+    ScheduleImage image;
+
+    // device state (created at the first decode)
+    int device = -1;
+    int32_t *d_image = nullptr;
+    size_t image_bytes = 0;
+    void *d_msgs = nullptr;       // message scratch
+    size_t msgs_bytes = 0;
+    float *d_post = nullptr;      // posterior scratch when the caller passes no llr_post
+    size_t post_bytes = 0;
+    // staging buffers of qcmet_decode_host
+    void *d_io = nullptr;
+    size_t io_bytes = 0;
+};
+
+// Host builder (layout.cpp).  Returns a QCMET status; fills `err` on failure.
+int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb, int32_t Z,
+               int32_t merge_mode, Code &code, std::string &err);
+
+// Message slot stride in elements: Z rounded up so that every slot starts on
+// a 16-byte boundary for every message format.
+inline size_t slot_stride(int32_t Z) { return (static_cast<size_t>(Z) + 15) & ~static_cast<size_t>(15); }
+
+// Kernel launch arguments (decode.cu).
+struct DecodeArgs {
+    const float *ch;         // [K][n]
+    const uint8_t *syn;      // [K][m]
+    float *post;             // [K][n] posteriors (the caller's llr_post or scratch)
+    void *msgs;              // [K][msg_slots][slot_stride] messages
+    uint8_t *hard;           // [K][n]
+    uint8_t *ok;             // [K]
+    const int32_t *image;    // schedule image (device)
+    int32_t image_words;
+    int32_t K, T, Z, n, m, nb;
+    int32_t msg_slots;
+    int64_t slot_stride;     // elements
+};
+
+// Launch the fused decode kernel for one message format (decode.cu).
+int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
+                  std::string &err);
+
+}  // namespace qcmet

@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA decoder (through the C ABI) against the FP64 oracle.
+
+Bars (the FP32 decoder): posterior LLRs within 1e-4 * max(|L_ref|, 1) over
+iterations 1-5; the ok flag equal to [H c = s] recomputed from the GPU's own
+hard decisions; at 50 iterations at least 99.99% of hard decisions and 99% of
+frame outcomes equal to the oracle's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import helpers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LLR_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2004_09084_gb300 import build
+    build.build()
+    import paper_2004_09084_gb300 as q
+    assert torch.cuda.is_available()
+    return q
+
+
+def gpu_decode(q, code, llr, syn, T, merge="exact", msg="fp32", threads=0, want_post=True):
+    qc = code if isinstance(code, q.Code) else q.Code(code.base, code.shifts, code.Z, merge=merge)
+    d_llr = torch.from_numpy(np.ascontiguousarray(llr)).cuda()
+    d_syn = torch.from_numpy(np.ascontiguousarray(syn)).cuda()
+    h, p, ok = q.decode(qc, d_llr, d_syn, T, msg=msg, threads=threads, want_post=want_post)
+    torch.cuda.synchronize()
+    return h.cpu().numpy(), (p.cpu().numpy() if p is not None else None), ok.cpu().numpy()
+
+
+def rel_err(a, ref):
+    return np.abs(a.astype(np.float64) - ref) / np.maximum(np.abs(ref), 1.0)
+
+
+def syndrome_ok(code, hard, syn):
+    return np.all(synth.syndrome(code, hard) == syn, axis=1).astype(np.uint8)
+
+
+# --------------------------------------------------------------------------
+# Small workload: rate 0.1, Z = 64, SNR 0.161
+
+@pytest.fixture(scope="module")
+def small():
+    code = synth.make_code("0.1", 64)
+    fr = synth.make_frames(code, 16, 0.161)
+    return code, fr
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 4, 5])
+def test_llr_parity_first_five_iterations(q, small, T):
+    code, fr = small
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, T)
+    rh, rp, rok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, T, nthreads=8)
+    err = rel_err(p, rp)
+    assert err.max() <= LLR_TOL, f"max relative LLR error {err.max():.3g}"
+    confident = np.abs(rp) > 1e-3
+    np.testing.assert_array_equal(h[confident], rh[confident])
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+
+
+def test_fifty_iterations_hard_decisions_and_frame_outcomes(q, small):
+    code, fr = small
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 50)
+    rh, rp, rok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 50, nthreads=8)
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))     # bit-exact flag
+    agree = np.mean(h == rh)
+    assert agree >= 0.9999, f"hard-decision agreement {agree:.6f}"
+    assert np.mean(ok == rok) >= 0.99
+
+
+def test_noiseless_frames_decode(q):
+    code = synth.make_code("0.1", 64)
+    fr = synth.make_frames(code, 4, 0.161, noiseless=True)
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 1)
+    np.testing.assert_array_equal(h, fr.x)
+    np.testing.assert_array_equal(ok, np.ones(4, np.uint8))
+
+
+def test_zero_iterations_return_the_channel(q, small):
+    code, fr = small
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 0)
+    np.testing.assert_array_equal(p, fr.llr)
+    np.testing.assert_array_equal(h, (fr.llr < 0).astype(np.uint8))
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+
+
+def test_coset_symmetry_is_exact_on_gpu(q, small):
+    code, fr = small
+    rng = np.random.default_rng(4)
+    x0 = rng.integers(0, 2, size=fr.x.shape, dtype=np.uint8)
+    flip = (1.0 - 2.0 * x0).astype(np.float32)
+    _, p, _ = gpu_decode(q, code, fr.llr, fr.syn, 7)
+    _, p2, _ = gpu_decode(q, code, fr.llr * flip, fr.syn ^ synth.syndrome(code, x0), 7)
+    np.testing.assert_array_equal(p2, p * flip)
+
+
+# --------------------------------------------------------------------------
+# Several thread-block passes with a ragged tail; more frames than SMs
+
+def test_parity_with_ragged_z(q):
+    code = synth.make_code("0.1", 2500)     # the paper's expansion factor; 2500 = 2 * 1024 + 452
+    fr = synth.make_frames(code, 3, 0.161)
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 3)
+    _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 3, nthreads=3)
+    assert rel_err(p, rp).max() <= LLR_TOL
+
+
+def test_more_frames_than_ctas(q):
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    code = synth.make_code("0.1", 8)
+    fr = synth.make_frames(code, sms + 9, 0.161)
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 4)
+    rh, rp, rok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 4, nthreads=8)
+    assert rel_err(p, rp).max() <= LLR_TOL
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+
+
+@pytest.mark.parametrize("threads", [32, 96, 256, 1024])
+def test_block_size_does_not_change_results(q, small, threads):
+    code, fr = small
+    ref = gpu_decode(q, code, fr.llr, fr.syn, 5)
+    got = gpu_decode(q, code, fr.llr, fr.syn, 5, threads=threads)
+    for a, b in zip(ref, got):
+        np.testing.assert_array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Code shapes: high-degree rows (lane-pair path), degenerate blocks
+
+def random_code(seed, mb, nb, Z, min_deg, max_deg):
+    rng = np.random.default_rng(seed)
+    base = np.zeros((mb, nb), np.int8)
+    for l in range(mb):
+        d = int(rng.integers(min_deg, max_deg + 1))
+        base[l, rng.choice(nb, d, replace=False)] = 1
+    shifts = np.where(base == 1, rng.integers(0, Z, size=base.shape), 0).astype(np.int32)
+    return synth.Code(base=base, shifts=shifts, Z=Z)
+
+
+@pytest.mark.parametrize("seed,lo,hi", [(0, 9, 12), (1, 13, 16), (2, 1, 16), (3, 2, 8)])
+def test_parity_for_row_degrees_up_to_the_limit(q, seed, lo, hi):
+    code = random_code(seed, 6, 18, 37, lo, hi)
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 2, size=(3, code.n), dtype=np.uint8)
+    llr = ((1.0 - 2.0 * x) * 2.0 + rng.normal(0, 2.0, size=x.shape)).astype(np.float32)
+    syn = synth.syndrome(code, x)
+    for merge in ("none", "exact"):
+        h, p, ok = gpu_decode(q, code, llr, syn, 3, merge=merge)
+        _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, llr, syn, 3)
+        assert rel_err(p, rp).max() <= LLR_TOL
+        np.testing.assert_array_equal(ok, syndrome_ok(code, h, syn))
+
+
+def test_degenerate_blocks(q):
+    # column 3 unconnected, row 2 empty (its checks only test s_m), row 3 a
+    # single circulant (degree-1 check), columns 4 and 5 of degree one
+    base = np.array([[1, 1, 1, 0, 1, 0],
+                     [1, 1, 0, 0, 0, 1],
+                     [0, 0, 0, 0, 0, 0],
+                     [0, 0, 1, 0, 0, 0]], np.int8)
+    Z = 33
+    rng = np.random.default_rng(8)
+    shifts = np.where(base == 1, rng.integers(0, Z, size=base.shape), 0).astype(np.int32)
+    code = synth.Code(base=base, shifts=shifts, Z=Z)
+    x = rng.integers(0, 2, size=(2, code.n), dtype=np.uint8)
+    llr = ((1.0 - 2.0 * x) + rng.normal(0, 1.0, size=x.shape)).astype(np.float32)
+    syn = synth.syndrome(code, x)
+    syn[1, 2 * Z + 5] ^= 1          # an empty check with s_m = 1 can never be satisfied
+    for T in (0, 1, 4):
+        h, p, ok = gpu_decode(q, code, llr, syn, T)
+        rh, rp, rok = oracle.decode(base, shifts, Z, llr, syn, T)
+        assert rel_err(p, rp).max() <= LLR_TOL
+        np.testing.assert_array_equal(ok, syndrome_ok(code, h, syn))
+        assert ok[1] == 0
+        np.testing.assert_array_equal(p[:, 3 * Z:4 * Z], llr[:, 3 * Z:4 * Z])
+
+
+# --------------------------------------------------------------------------
+# Schedules (Results, Eqs. (m)-(m2))
+
+def test_exact_merge_is_bit_identical_to_base_order(q, small):
+    code, fr = small
+    a = gpu_decode(q, code, fr.llr, fr.syn, 6, merge="none")
+    b = gpu_decode(q, code, fr.llr, fr.syn, 6, merge="exact")
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+
+
+def test_greedy_merge_matches_the_oracle_in_the_same_order(q, small):
+    code, fr = small
+    qc = q.Code(code.base, code.shifts, code.Z, merge="greedy")
+    rows, layers = qc.schedule()
+    assert len(layers) < 54
+    h, p, ok = gpu_decode(q, qc, fr.llr, fr.syn, 4)
+    _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 4, order=rows,
+                             nthreads=8)
+    assert rel_err(p, rp).max() <= LLR_TOL
+
+
+# --------------------------------------------------------------------------
+# Entry points and error paths
+
+def test_without_llr_post_the_outputs_are_unchanged(q, small):
+    code, fr = small
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 5)
+    h2, p2, ok2 = gpu_decode(q, code, fr.llr, fr.syn, 5, want_post=False)
+    assert p2 is None
+    np.testing.assert_array_equal(h, h2)
+    np.testing.assert_array_equal(ok, ok2)
+
+
+def test_host_entry_point_matches_device_entry_point(q, small):
+    code, fr = small
+    qc = q.Code(code.base, code.shifts, code.Z)
+    h, p, ok = gpu_decode(q, qc, fr.llr, fr.syn, 5)
+    h2, p2, ok2 = q.decode_host(qc, fr.llr, fr.syn, 5)
+    np.testing.assert_array_equal(h, h2)
+    np.testing.assert_array_equal(p, p2)
+    np.testing.assert_array_equal(ok, ok2)
+    h3, p3, ok3 = q.decode_host(qc, fr.llr, fr.syn, 5, want_post=False)
+    assert p3 is None
+    np.testing.assert_array_equal(h, h3)
+
+
+def test_misaligned_pointer_is_rejected(q, small):
+    code, fr = small
+    qc = q.Code(code.base, code.shifts, code.Z)
+    buf = torch.from_numpy(np.concatenate([np.zeros(1, np.float32), fr.llr[0]])).cuda()
+    syn = torch.from_numpy(fr.syn[:1]).cuda()
+    hard = torch.empty((1, code.n), dtype=torch.uint8, device="cuda")
+    ok = torch.empty((1,), dtype=torch.uint8, device="cuda")
+    st = q.lib.qcmet_decode(qc.handle, buf.data_ptr() + 4, syn.data_ptr(), 1, 3,
+                            hard.data_ptr(), None, ok.data_ptr(), None)
+    assert st == q.ERR_ALIGNMENT
+    assert b"aligned" in q.lib.qcmet_last_error()
+
+
+def test_invalid_sizes_are_rejected(q, small):
+    code, fr = small
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d = torch.zeros((1, code.n), dtype=torch.float32, device="cuda")
+    s = torch.zeros((1, code.m), dtype=torch.uint8, device="cuda")
+    h = torch.zeros((1, code.n), dtype=torch.uint8, device="cuda")
+    o = torch.zeros((1,), dtype=torch.uint8, device="cuda")
+    args = (qc.handle, d.data_ptr(), s.data_ptr())
+    assert q.lib.qcmet_decode(*args, -1, 3, h.data_ptr(), None, o.data_ptr(), None) == q.ERR_INVALID_ARG
+    assert q.lib.qcmet_decode(*args, 1, -1, h.data_ptr(), None, o.data_ptr(), None) == q.ERR_INVALID_ARG
+    assert q.lib.qcmet_decode(*args, 0, 3, None, None, None, None) == q.OK      # K = 0: no-op
+    with pytest.raises(q.QcmetError):
+        q.decode(qc, d, s, 3, threads=48)
+
+
+# --------------------------------------------------------------------------
+# Full size: Z = 12500 (n = 10^6), 128 frames, the configuration bench.py times
+
+@pytest.fixture(scope="module")
+def full():
+    code = synth.make_code("0.1", 12500)
+    fr = synth.make_frames(code, 128, 0.161)
+    return code, fr
+
+
+def test_full_size_llr_parity_on_sampled_frames(q, full):
+    code, fr = full
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 2)
+    pick = [0, 77]
+    _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr[pick], fr.syn[pick], 2,
+                             nthreads=2)
+    assert rel_err(p[pick], rp).max() <= LLR_TOL
+
+
+def test_full_size_fixed_iterations_properties(q, full):
+    code, fr = full
+    h, p, ok = gpu_decode(q, code, fr.llr, fr.syn, 100)
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+    np.testing.assert_array_equal(h, (p < 0).astype(np.uint8))
+    assert np.all(np.isfinite(p))
+    # decoding a coset-shifted copy negates exactly the shifted posteriors
+    x0 = fr.x[::-1].copy()
+    flip = (1.0 - 2.0 * x0).astype(np.float32)
+    _, p2, ok2 = gpu_decode(q, code, fr.llr * flip, fr.syn ^ synth.syndrome(code, x0), 100)
+    # exact up to a q that is exactly 0 (its check then sends +-Phi(30) ~ 2e-13 either way)
+    np.testing.assert_allclose(p2, p * flip, rtol=1.2e-7, atol=1e-9)
+    np.testing.assert_array_equal(ok2, ok)
