@@ -189,6 +189,10 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 
+def progress(msg: str):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -219,9 +223,11 @@ def run_ours(args):
         q.decode(qc, llr, syn, ITERS, hard=hard, llr_post=post, ok=ok, msg=args.msg,
                  stream=stream)
 
+    progress("inputs resident; warm-up")
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
+    progress("timed region")
 
     def barrier():
         if world > 1:
@@ -244,6 +250,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     clocks = clk.summary()
+    progress(f"timed region done: {ms:.2f} ms/step; end-to-end leg")
 
     # decode quality of the last step (outside the timed region)
     h_cpu = hard.cpu().numpy()
@@ -286,6 +293,7 @@ def run_ours(args):
     deg1_edges = code.edges - core_edges
     state_bytes = (core_edges * (8 + 2 * mbytes) + deg1_edges * 4) * K_FRAMES * ITERS
 
+    progress("end-to-end leg done")
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -334,9 +342,11 @@ def run_profile(args):
     dev = torch.device("cuda", 0)
     llr = torch.from_numpy(fr.llr).to(dev)
     syn = torch.from_numpy(fr.syn).to(dev)
-    for _ in range(args.launches):
+    progress("profile case: inputs resident")
+    for k in range(args.launches):
         hard, post, ok = q.decode(qc, llr, syn, args.iters, msg=args.msg)
-    torch.cuda.synchronize(dev)
+        torch.cuda.synchronize(dev)
+        progress(f"profile case: launch {k} done")
     print(json.dumps({"profile_case": {"frames": args.frames, "iters": args.iters,
                                        "launches": args.launches, "msg": args.msg,
                                        "ok_rate": float(ok.float().mean().item())}}))

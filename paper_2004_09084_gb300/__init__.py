@@ -108,6 +108,7 @@ def library_path() -> str:
     return _LIB_PATH
 
 
+
 class Code:
     """A QC-MET-LDPC code: base matrix (1 = circulant), shifts and Z."""
 

@@ -17,6 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqcmet.so")
+# Diagnostic variant: every device access is bounds- and alignment-checked and
+# a violation is recorded and skipped instead of touching memory.
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libqcmet_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["layout.cpp", "api.cpp", "decode.cu"]
@@ -39,15 +43,16 @@ def _deps():
     return paths
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra, build_dir: str) -> str:
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -55,33 +60,39 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    """Compile and link the library; returns its path.
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Compile and link the library (or its checked variant); returns its path.
 
-    Holds an exclusive lock on ``_build/.lock`` so that processes that start
+    Holds an exclusive lock on the build folder so that processes that start
     together (one per GPU) build once.
     """
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    with open(os.path.join(BUILD, ".lock"), "w") as lock:
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD_CHECKED if checked else BUILD
+    if not force and up_to_date(checked):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
+    with open(os.path.join(bdir, ".lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
-        if not force and up_to_date():
-            return LIB
-        return _build_locked(verbose_ptxas)
+        if not force and up_to_date(checked):
+            return lib
+        return _build_locked(verbose_ptxas, checked)
 
 
-def _build_locked(verbose_ptxas: bool) -> str:
+def _build_locked(verbose_ptxas: bool, checked: bool = False) -> str:
+    LIBP = LIB_CHECKED if checked else LIB
+    bdir = BUILD_CHECKED if checked else BUILD
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    defs = ["-DQCMET_DEVICE_CHECKS"] if checked else []
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra if s.endswith(".cu") else []), SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(
+            lambda s: _compile(s, defs + (extra if s.endswith(".cu") else []), bdir), SOURCES))
+    tmp = LIBP + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, LIBP)
+    return LIBP
 
 
 if __name__ == "__main__":

@@ -202,7 +202,7 @@ __device__ __forceinline__ float gather_q(const int4 &en, int i, const Frame<M> 
     int j = i + en.y;
     j = j >= Z ? j - Z : j;
     const int v = en.x + j;
-    if (en.z < 0) return fr.ch[v];  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
+    if (en.z < 0) return __ldcs(fr.ch + v);  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
     const float lv = fr.post[v];
     const float ro = first ? 0.0f : Msg<M>::load(fr.msg + (size_t)en.z * stride + i);
     return lv - ro;
@@ -232,29 +232,64 @@ __device__ __forceinline__ float u_of(float q) {
     return exp2f(-kLog2e * fminf(fabsf(q), kClipMax));
 }
 
-// Rows of degree D <= 8: one thread per check.
+// Rows of degree D <= 4: one thread per check.  Each thread first gathers the
+// inputs of U checks (i, i + NT, ..., i + (U-1) NT) in straight-line code --
+// the source array of an edge is selected, not branched on, and checks past Z
+// load from a clamped (valid) index -- so that all U * (2D + 1) loads are in
+// flight together; then it computes and writes the U checks.
 //   first: iteration 0 (old messages are zero and are not read)
 //   last : final iteration (degree-1 variables get their posterior)
+#ifndef QCMET_BATCH_LOW
+#define QCMET_BATCH_LOW 2
+#endif
+template <int D>
+__host__ __device__ constexpr int batch_of() { return QCMET_BATCH_LOW; }
+
 template <int D, typename M>
 __device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_base,
                                         const Frame<M> &fr, int Z, size_t stride, bool first,
                                         bool last) {
-    for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-        float q[D], u[D];
-        unsigned par = fr.syn[check_base + i] & 1u;
+    constexpr int U = batch_of<D>();
+    const int step = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
+        float lv[U][D], ro[U][D];
+        unsigned par[U];
 #pragma unroll
-        for (int e = 0; e < D; ++e) {
-            q[e] = gather_q<M>(ent[e], i, fr, Z, stride, first);
-            par ^= q[e] < 0.0f ? 1u : 0u;
-            u[e] = u_of(q[e]);
+        for (int k = 0; k < U; ++k) {
+            const int i = min(i0 + k * step, Z - 1);
+            par[k] = fr.syn[check_base + i] & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const int4 en = ent[e];
+                int j = i + en.y;
+                j = j >= Z ? j - Z : j;
+                // degree-1 variable: L_qn - L_rmn(old) is the channel LLR exactly
+                const float *src = en.z < 0 ? fr.ch : fr.post;
+                lv[k][e] = src[en.x + j];
+                const bool has_old = !first && en.z >= 0;
+                ro[k][e] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + i) : 0.0f;
+            }
         }
-        exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
-            scatter_r<M>(ent[e], i, q[e], a, b, par, fr, Z, stride, last);
-        });
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = i0 + k * step;
+            if (i >= Z) break;
+            float q[D], u[D];
+            unsigned p = par[k];
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                q[e] = lv[k][e] - ro[k][e];
+                p ^= q[e] < 0.0f ? 1u : 0u;
+                u[e] = u_of(q[e]);
+            }
+            exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+                scatter_r<M>(ent[e], i, q[e], a, b, p, fr, Z, stride, last);
+            });
+        }
     }
 }
 
-// Rows of degree 9..16: two lanes per check (lanes l and l ^ 16 of a warp).
+// Rows of degree 5..16: two lanes per check (lanes l and l ^ 16 of a warp).
 // Each lane owns E = ceil(D/2) edges; the lanes swap their partial products
 // and sign parities with one shuffle each.
 template <int D, typename M>
@@ -316,10 +351,10 @@ __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int ch
         QCMET_ROW_CASE(2)
         QCMET_ROW_CASE(3)
         QCMET_ROW_CASE(4)
-        QCMET_ROW_CASE(5)
-        QCMET_ROW_CASE(6)
-        QCMET_ROW_CASE(7)
-        QCMET_ROW_CASE(8)
+        QCMET_PAIR_CASE(5)
+        QCMET_PAIR_CASE(6)
+        QCMET_PAIR_CASE(7)
+        QCMET_PAIR_CASE(8)
         QCMET_PAIR_CASE(9)
         QCMET_PAIR_CASE(10)
         QCMET_PAIR_CASE(11)

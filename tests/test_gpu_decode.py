@@ -290,3 +290,39 @@ def test_full_size_fixed_iterations_properties(q, full):
     # exact up to a q that is exactly 0 (its check then sends +-Phi(30) ~ 2e-13 either way)
     np.testing.assert_allclose(p2, p * flip, rtol=1.2e-7, atol=1e-9)
     np.testing.assert_array_equal(ok2, ok)
+
+
+# --------------------------------------------------------------------------
+# 16-bit message storage (FP32 arithmetic and posteriors)
+#
+# The oracle rounds every stored message to the same format (IEEE round to
+# nearest even).  FP32 and FP64 messages can straddle a rounding midpoint, so
+# a stored message may differ by one unit in the last place of the 16-bit
+# format, about 2^(1-p) |r| for a p-bit significand; such differences add up
+# over iterations.  Bound: T * 2^(2-p) relative (floor 1).
+
+@pytest.mark.parametrize("msg,p,fmt", [("fp16", 11, oracle.MSG_FP16), ("bf16", 8, oracle.MSG_BF16)])
+def test_16bit_messages_match_the_oracle_with_rounded_messages(q, small, msg, p, fmt):
+    code, fr = small
+    for T in (1, 3, 5):
+        h, pg, ok = gpu_decode(q, code, fr.llr, fr.syn, T, msg=msg)
+        _, rp, rok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, T,
+                                   msg_fmt=fmt, nthreads=8)
+        err = rel_err(pg, rp)
+        assert err.max() <= T * 2.0 ** (2 - p), f"T={T}: {err.max():.3g}"
+        assert np.mean(h == (rp < 0)) >= 0.999
+        np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+
+
+@pytest.mark.parametrize("msg", ["fp16", "bf16"])
+def test_16bit_messages_keep_frame_outcomes(q, msg):
+    # at an SNR where about half the frames decode, the 16-bit decoders reach the
+    # same frame outcome as the FP32 decoder on (nearly) every frame
+    code = synth.make_code("0.1", 64)
+    fr = synth.make_frames(code, 64, 0.2)
+    h32, _, ok32 = gpu_decode(q, code, fr.llr, fr.syn, 50)
+    h16, _, ok16 = gpu_decode(q, code, fr.llr, fr.syn, 50, msg=msg)
+    assert np.mean(ok16 == ok32) >= 0.95
+    fer32 = np.mean(np.any(h32 != fr.x, axis=1))
+    fer16 = np.mean(np.any(h16 != fr.x, axis=1))
+    assert abs(fer16 - fer32) <= 0.05
