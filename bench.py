@@ -189,6 +189,27 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 
+def frame_offset(rank: int, frames_per_rank: int) -> int:
+    """First frame index of a rank: ranks decode disjoint frame sets (weak scaling)."""
+    return rank * frames_per_rank
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    """Step time of the whole job: the slowest rank's (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mbit_per_s(world: int, frames_per_rank: int, n: int, seconds: float) -> float:
+    """Whole-job decoded Mbit/s: all ranks' bits over the slowest rank's time."""
+    return world * frames_per_rank * n / seconds / 1e6
+
+
 def progress(msg: str):
     print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
 
@@ -210,7 +231,7 @@ def run_ours(args):
 
     code = synth.make_code(RATE, Z)
     qc = q.Code(code.base, code.shifts, code.Z)
-    fr = synth.make_frames(code, K_FRAMES, SNR, first=rank * K_FRAMES)
+    fr = synth.make_frames(code, K_FRAMES, SNR, first=frame_offset(rank, K_FRAMES))
     n = code.n
     llr = torch.from_numpy(fr.llr).to(dev)
     syn = torch.from_numpy(fr.syn).to(dev)
@@ -244,11 +265,7 @@ def run_ours(args):
         end.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
-    ms = start.elapsed_time(end) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(start.elapsed_time(end) / args.steps, dev)
     clocks = clk.summary()
     progress(f"timed region done: {ms:.2f} ms/step; end-to-end leg")
 
@@ -272,16 +289,12 @@ def run_ours(args):
     for _ in range(e2e_steps):
         q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
                       stream=stream, out=host_out)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     h2d = K_FRAMES * n * 4 + K_FRAMES * code.m
     d2h = K_FRAMES * n + K_FRAMES
 
     bits = world * K_FRAMES * n
-    value = bits / (ms * 1e-3) / 1e6
+    value = job_mbit_per_s(world, K_FRAMES, n, ms * 1e-3)
     peak, peak_kind = peaks()
     algo_bytes = BYTES_PER_EDGE[args.msg] * code.edges * K_FRAMES * ITERS
     achieved = algo_bytes / (ms * 1e-3) / 1e9
@@ -313,7 +326,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (message state "
                              f"{K_FRAMES * info['msg_slots'] * Z * mbytes / 1e9:.2f} GB per GPU)"},
             "fer": fer, "ok_rate": ok_rate,
-            "e2e": {"value": bits / e2e_s / 1e6, "unit": "Mbit/s",
+            "e2e": {"value": job_mbit_per_s(world, K_FRAMES, n, e2e_s), "unit": "Mbit/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
