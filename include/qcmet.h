@@ -158,6 +158,42 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
                       int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
                       const qcmet_decode_options *opts, void *stream);
 
+/*
+ * qcmet_decode with FP32 messages for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is a service of this library.
+ *
+ * Who needs it: code that must not call cudaMalloc -- for example a
+ * reconciliation pipeline that keeps several streams busy and cannot afford
+ * the device-wide synchronisation an allocation implies, or a plug-in whose
+ * host application owns all device memory through its own pool.
+ * qcmet_decode allocates scratch on a handle's first use (and when K grows);
+ * this call allocates nothing: it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Its scratch is one fixed array of 32 MiB that the library defines in device
+ * memory; every GPU that loads the library holds it until the process exits.
+ * 64 KiB of it hold a copy of the code's layer table, the rest the messages:
+ * the call needs K * msg_slots * roundup(Z, 16) * 4 bytes of the remaining
+ * 32 MiB - 64 KiB and returns QCMET_ERR_INVALID_ARG, with a message that
+ * states both sizes, when that does not fit (e.g. at Z = 12500 and 230 slots
+ * it takes at most 2 frames per call; at Z = 64, over 500).
+ *
+ * Arguments, layouts and results are those of qcmet_decode, except that
+ * llr_post must not be NULL (it holds the posteriors while decoding) and no
+ * options are taken (FP32 messages, default block size).  The results equal
+ * qcmet_decode's bit for bit.
+ *
+ * All calls share the one array and it keeps what the last call left; this
+ * call rewrites everything it reads before reading it.  Calls whose work can
+ * overlap on the GPU (different streams, or host threads) race on the array:
+ * order them on one stream.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture begins.
+ */
+int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                         int32_t K, int32_t iterations, uint8_t *hard, float *llr_post,
+                         uint8_t *ok, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qcmet_last_error(void);
 

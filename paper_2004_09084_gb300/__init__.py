@@ -43,7 +43,7 @@ MSG = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXPORTS = (
     "qcmet_code_create", "qcmet_code_create_ex", "qcmet_code_destroy", "qcmet_code_get_info",
     "qcmet_code_get_schedule", "qcmet_decode", "qcmet_decode_ex", "qcmet_decode_host",
-    "qcmet_last_error", "qcmet_status_string", "qcmet_version",
+    "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
 )
 
 
@@ -84,6 +84,7 @@ def _load():
     lib.qcmet_decode.argtypes = dec + [vp]
     lib.qcmet_decode_ex.argtypes = dec + [ctypes.POINTER(DecodeOptions), vp]
     lib.qcmet_decode_host.argtypes = dec + [ctypes.POINTER(DecodeOptions), vp]
+    lib.qcmet_decode_noalloc.argtypes = dec + [vp]
     lib.qcmet_last_error.argtypes = []
     lib.qcmet_last_error.restype = ctypes.c_char_p
     lib.qcmet_status_string.argtypes = [ctypes.c_int]

@@ -283,6 +283,45 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
     return QCMET_OK;
 }
 
+int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                         int32_t K, int32_t iterations, uint8_t *hard, float *llr_post,
+                         uint8_t *ok, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    if (K < 0) return fail(QCMET_ERR_INVALID_ARG, "K must be >= 0");
+    if (iterations < 0) return fail(QCMET_ERR_INVALID_ARG, "iterations must be >= 0");
+    if (K == 0) return QCMET_OK;
+    if (!llr_ch || !syndrome || !hard || !llr_post || !ok)
+        return fail(QCMET_ERR_INVALID_ARG,
+                    "llr_ch, syndrome, hard, llr_post and ok must not be NULL "
+                    "(qcmet_decode_noalloc keeps the posteriors in llr_post)");
+    if (!aligned16(llr_ch) || !aligned16(syndrome) || !aligned16(hard) || !aligned16(ok) ||
+        !aligned16(llr_post))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    const qcmet::Code &c = code->c;
+    qcmet::DecodeArgs a;
+    a.ch = llr_ch;
+    a.syn = syndrome;
+    a.post = llr_post;
+    a.msgs = nullptr;   // set by the launcher: inside the static scratch
+    a.hard = hard;
+    a.ok = ok;
+    a.image = nullptr;  // set by the launcher: a copy inside the static scratch
+    a.image_words = (int32_t)c.image.words.size();
+    a.K = K;
+    a.T = iterations;
+    a.Z = c.Z;
+    a.n = c.nb * c.Z;
+    a.m = c.mb * c.Z;
+    a.nb = c.nb;
+    a.msg_slots = c.msg_slots;
+    a.slot_stride = (int64_t)qcmet::slot_stride(c.Z);
+    std::string err;
+    int st = qcmet::launch_decode_noalloc(a, c.image.words.data(),
+                                          c.image.words.size() * sizeof(int32_t), stream, err);
+    if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
 const char *qcmet_last_error(void) { return g_last_error.c_str(); }
 
 const char *qcmet_status_string(int status) {

@@ -38,6 +38,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <mutex>
 
 #include "qcmet_internal.h"
 
@@ -542,6 +543,86 @@ int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void
         case QCMET_MSG_BF16: return launch_typed<__nv_bfloat16>(a, threads, stream, err);
         default: err = "unknown message format"; return QCMET_ERR_INVALID_ARG;
     }
+}
+
+// ---- decoding without device allocations ----------------------------------
+//
+// Scratch for qcmet_decode_noalloc: one fixed-size array in device memory that
+// the library defines at file scope.  Every GPU that loads the library holds
+// it until the process exits.  Layout: the code's layer table in the first
+// kNoAllocImageBytes, the check-to-variable messages after it.  In host code
+// the name g_noalloc_scratch is only a stand-in for the symbol; its device
+// address comes from cudaGetSymbolAddress, taken once per device.
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;      // 32 MiB in total
+constexpr size_t kNoAllocImageBytes = size_t(64) << 10;  // 64 KiB of it for the layer table
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+int noalloc_address(void **out, std::string &err) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= 64) {
+        err = "device index above 63";
+        return QCMET_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e);
+            return QCMET_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return QCMET_OK;
+}
+
+}  // namespace
+
+size_t noalloc_capacity_bytes() { return kNoAllocBytes - kNoAllocImageBytes; }
+
+int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_bytes,
+                          void *stream, std::string &err) {
+    if (image_bytes > kNoAllocImageBytes) {
+        err = "the code's layer table needs " + std::to_string(image_bytes) +
+              " bytes; qcmet_decode_noalloc reserves " + std::to_string(kNoAllocImageBytes);
+        return QCMET_ERR_INVALID_ARG;
+    }
+    const size_t need = (size_t)a.K * (size_t)a.msg_slots * (size_t)a.slot_stride * sizeof(float);
+    if (need > noalloc_capacity_bytes()) {
+        err = "decoding these frames needs " + std::to_string(need) +
+              " bytes of message scratch; qcmet_decode_noalloc holds " +
+              std::to_string(noalloc_capacity_bytes()) + " (use fewer frames per call or qcmet_decode)";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    void *base = nullptr;
+    int st = noalloc_address(&base, err);
+    if (st) return st;
+    char *p = static_cast<char *>(base);
+    // The layer table is copied in every call: the array keeps whatever the
+    // previous call left there.  The messages need no clearing (the first
+    // iteration does not read them).
+    cudaError_t e = cudaMemcpyAsync(p, image_host, image_bytes, cudaMemcpyHostToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemcpyAsync(layer table): ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    a.image = reinterpret_cast<const int32_t *>(p);
+    a.msgs = p + kNoAllocImageBytes;
+    return launch_typed<float>(a, kDefaultThreads, stream, err);
 }
 
 }  // namespace qcmet

@@ -113,4 +113,10 @@ struct DecodeArgs {
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
                   std::string &err);
 
+// Launch the FP32 decode kernel with its messages and layer table in the
+// library's static device scratch (decode.cu): no device allocation.
+int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_bytes,
+                          void *stream, std::string &err);
+size_t noalloc_capacity_bytes();
+
 }  // namespace qcmet
