@@ -366,6 +366,77 @@ def run_profile(args):
     return 0
 
 
+def run_report(args):
+    """Secondary measurements printed as one JSON line per case (not the bench line)."""
+    import torch
+
+    import paper_2004_09084_gb300 as q
+    dev = torch.device("cuda", 0)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / reps, out
+
+    if args.report == "early-stop":
+        # Discussion, Table tabearly: fixed iterations against early termination
+        code = synth.make_code(RATE, Z)
+        qc = q.Code(code.base, code.shifts, code.Z)
+        T = args.iters if args.iters != ITERS else 50
+        for snr in (0.161, 0.2, 0.22, 0.25):
+            fr = synth.make_frames(code, K_FRAMES, snr, first=50_000)
+            llr = torch.from_numpy(fr.llr).to(dev)
+            syn = torch.from_numpy(fr.syn).to(dev)
+            ms_fix, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T))
+            fer_fix = float(np.mean(np.any(h.cpu().numpy() != fr.x, axis=1)))
+            for every in (1, 5):
+                ms_et, (h2, _, ok2, it) = timed(lambda: q.decode_early_stop(qc, llr, syn, T, every))
+                it = it.cpu().numpy()
+                print(json.dumps({
+                    "report": "early-stop", "snr": snr, "max_iterations": T, "check_every": every,
+                    "fixed": {"ms": ms_fix, "mbit_s": K_FRAMES * code.n / ms_fix / 1e3, "fer": fer_fix},
+                    "early": {"ms": ms_et, "mbit_s": K_FRAMES * code.n / ms_et / 1e3,
+                              "fer": float(np.mean(np.any(h2.cpu().numpy() != fr.x, axis=1))),
+                              "avg_iterations": float(it.mean()), "max_iterations_used": int(it.max())},
+                }), flush=True)
+        return 0
+
+    if args.report == "precision":
+        # 16-bit message storage: rates 0.1 / 0.05 / 0.02 at their SNRs, against the FP64 oracle
+        import oracle
+        plan = [("0.1", 100), ("0.05", 75), ("0.02", 100)]
+        for rate, T in plan:
+            code = synth.make_code(rate, Z)
+            snr = synth.RATE_SNR[rate]
+            qc = q.Code(code.base, code.shifts, code.Z)
+            fr = synth.make_frames(code, K_FRAMES, snr, first=60_000)
+            llr = torch.from_numpy(fr.llr).to(dev)
+            syn = torch.from_numpy(fr.syn).to(dev)
+            _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr[:1], fr.syn[:1], 5)
+            for msg in ("fp32", "fp16", "bf16"):
+                ms, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T, msg=msg))
+                hn = h.cpu().numpy()
+                _, p5, _ = q.decode(qc, llr[:1], syn[:1], 5, msg=msg)
+                p5 = p5.cpu().numpy().astype(np.float64)[0]
+                err = np.abs(p5 - rp[0]) / np.maximum(np.abs(rp[0]), 1.0)
+                print(json.dumps({
+                    "report": "precision", "rate": rate, "snr": snr, "iterations": T, "msg": msg,
+                    "edges": code.edges, "ms": ms, "mbit_s": K_FRAMES * code.n / ms / 1e3,
+                    "fer": float(np.mean(np.any(hn != fr.x, axis=1))), "ber": float(np.mean(hn != fr.x)),
+                    "ok_rate": float(ok.float().mean().item()),
+                    "llr_err_vs_fp64_T5": {"max": float(err.max()), "p999": float(np.quantile(err, 0.999)),
+                                           "hard_agree": float(np.mean((p5 < 0) == (rp[0] < 0)))},
+                }), flush=True)
+        return 0
+    raise SystemExit(f"unknown report {args.report}")
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -379,7 +450,11 @@ def main():
     ap.add_argument("--frames", type=int, default=K_FRAMES)
     ap.add_argument("--iters", type=int, default=ITERS)
     ap.add_argument("--launches", type=int, default=2)
+    ap.add_argument("--report", choices=["early-stop", "precision"],
+                    help="print secondary measurements instead of the bench line")
     args = ap.parse_args()
+    if args.report:
+        return run_report(args)
     if args.profile:
         return run_profile(args)
     if args.warmup < 3 and args.impl == "ours":

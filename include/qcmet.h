@@ -148,6 +148,22 @@ int qcmet_decode_ex(const qcmet_code *code, const float *llr_ch, const uint8_t *
                     const qcmet_decode_options *opts, void *stream);
 
 /*
+ * qcmet_decode_ex with early termination (Discussion, Table tabearly): after
+ * every check_every-th iteration each frame takes its hard decision and tests
+ * H c = s; a frame that passes stops there.  Frames are independent, so each
+ * stops on its own.  A stopped frame's outputs equal those of a fixed decode
+ * of exactly iterations_used[k] iterations.
+ *   max_iterations : >= 0, the iteration limit (the last iteration is always tested)
+ *   check_every    : >= 1; each test costs about a fifth of an iteration
+ *   iterations_used: device [K] int32 out, iterations each frame ran
+ * Other arguments, errors and scratch as qcmet_decode_ex.
+ */
+int qcmet_decode_early_stop(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                            int32_t K, int32_t max_iterations, int32_t check_every, uint8_t *hard,
+                            float *llr_post, uint8_t *ok, int32_t *iterations_used,
+                            const qcmet_decode_options *opts, void *stream);
+
+/*
  * qcmet_decode_ex for callers whose data live in host memory: every pointer
  * is a host pointer (pinned memory gives the fastest copies).  The call
  * copies the inputs to library-owned device buffers on `stream`, decodes,

@@ -75,7 +75,7 @@ def _load():
     lib.oracle_round_msg.restype = d
     lib.oracle_check_update.argtypes = [i, p, i, i, p]
     lib.oracle_check_update.restype = None
-    lib.oracle_decode.argtypes = [i, i, i, p, p, p, i, i, i, p, p, p, p, p, i, i, p, p, i]
+    lib.oracle_decode.argtypes = [i, i, i, p, p, p, i, i, i, p, p, p, p, p, i, i, p, p, i, i, p]
     lib.oracle_decode.restype = i
     _lib = lib
     return lib
@@ -113,13 +113,15 @@ def check_update(q, s: int = 0, rule: int = RULE_PHI) -> np.ndarray:
 
 def decode(base, shifts, Z: int, llr, syn, iterations: int, order=None,
            rule: int = RULE_PHI, msg_fmt: int = MSG_EXACT, w_scale=None, w_offset=None,
-           nthreads: int = 1):
+           nthreads: int = 1, early_every: int = 0, return_iters: bool = False):
     """Layered BP (Methods steps 1-4) on ``K`` frames.
 
-    Returns ``(hard uint8 [K, n], llr_post float64 [K, n], ok uint8 [K])``.
-    ``order`` is the sequence of base rows one iteration visits (default
-    ``0..mb-1``).  ``w_scale``/``w_offset`` are the min-sum weights with shape
-    ``[iterations, mb, 2]``.
+    Returns ``(hard uint8 [K, n], llr_post float64 [K, n], ok uint8 [K])``, plus
+    ``iters_used int32 [K]`` when ``return_iters``.  ``order`` is the sequence
+    of base rows one iteration visits (default ``0..mb-1``).  ``w_scale``/
+    ``w_offset`` are the min-sum weights with shape ``[iterations, mb, 2]``.
+    ``early_every > 0`` stops a frame after the first multiple of
+    ``early_every`` iterations at which ``H c = s`` (early termination).
     """
     base = np.ascontiguousarray(base, dtype=np.int8)
     shifts = np.ascontiguousarray(shifts, dtype=np.int32)
@@ -144,10 +146,13 @@ def decode(base, shifts, Z: int, llr, syn, iterations: int, order=None,
         wo = np.ascontiguousarray(w_offset, dtype=np.float64).reshape(-1)
         if ws.size < iterations * mb * 2 or wo.size < iterations * mb * 2:
             raise ValueError("min-sum weights must have shape [iterations, mb, 2]")
+    iters = np.empty((K,), dtype=np.int32)
     rc = _load().oracle_decode(mb, nb, int(Z), _ptr(base), _ptr(shifts), _ptr(ordr), n_order,
                                K, int(iterations), _ptr(llr), _ptr(syn), _ptr(hard), _ptr(post),
                                _ptr(ok), int(rule), int(msg_fmt), _ptr(ws), _ptr(wo),
-                               int(nthreads))
+                               int(nthreads), int(early_every), _ptr(iters))
     if rc != 0:
         raise ValueError(f"oracle_decode failed with status {rc}")
+    if return_iters:
+        return hard, post, ok, iters
     return hard, post, ok

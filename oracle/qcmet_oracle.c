@@ -250,6 +250,29 @@ static int graph_build(int mb, int nb, int Z, const int8_t *base, const int32_t 
 }
 
 /* ---------------------------------------------------------------------- */
+/* Step 4 and the syndrome test: hard decisions from L_qn, 1 iff H c = s.  */
+
+static int hard_and_test(const graph_t *g, const double *Lq, const uint8_t *syn, uint8_t *hard)
+{
+    const int Z = g->Z;
+    const int n = g->nb * Z;
+    for (int i = 0; i < n; ++i) hard[i] = Lq[i] >= 0.0 ? 0 : 1;   /* c_n = 0 iff L_qn >= 0 */
+    for (int l = 0; l < g->mb; ++l) {
+        const int c0 = g->row_first[l];
+        const int d = g->row_first[l + 1] - c0;
+        for (int i = 0; i < Z; ++i) {
+            int par = syn[l * Z + i] & 1;
+            for (int j = 0; j < d; ++j) {
+                const int k = c0 + j;
+                par ^= hard[g->circ_col[k] * Z + (i + g->circ_shift[k]) % Z];
+            }
+            if (par) return 0;
+        }
+    }
+    return 1;
+}
+
+/* ---------------------------------------------------------------------- */
 /* One frame of layered BP, steps 1-4.                                     */
 
 typedef struct {
@@ -261,10 +284,11 @@ typedef struct {
     int msg_fmt;
     const double *w_scale;  /* min-sum weights [T][mb][2] or NULL */
     const double *w_offset;
+    int early_every;        /* > 0: test H c = s after every early_every-th iteration */
 } decode_cfg_t;
 
 static int decode_frame(const decode_cfg_t *cfg, const float *llr_ch, const uint8_t *syn,
-                        uint8_t *hard, double *llr_post, uint8_t *ok)
+                        uint8_t *hard, double *llr_post, uint8_t *ok, int32_t *iters_used)
 {
     const graph_t *g = cfg->g;
     const int Z = g->Z;
@@ -286,7 +310,9 @@ static int decode_frame(const decode_cfg_t *cfg, const float *llr_ch, const uint
     /* step 1: L_qn = 2 R_n / sigma^2, supplied as the channel LLR */
     for (int i = 0; i < n; ++i) Lq[i] = (double)llr_ch[i];
 
-    for (int t = 0; t < cfg->T; ++t) {
+    int t_used = cfg->T;
+    int stopped = 0;
+    for (int t = 0; t < cfg->T && !stopped; ++t) {
         for (int oi = 0; oi < cfg->n_order; ++oi) {
             const int l = cfg->order[oi];
             const int c0 = g->row_first[l];
@@ -320,31 +346,19 @@ static int decode_frame(const decode_cfg_t *cfg, const float *llr_ch, const uint
                 }
             }
         }
-    }
-
-    /* step 4: hard decision, c_n = 0 iff L_qn >= 0 */
-    for (int i = 0; i < n; ++i) {
-        hard[i] = Lq[i] >= 0.0 ? 0 : 1;
-        if (llr_post) llr_post[i] = Lq[i];
-    }
-    /* syndrome flag: 1 iff H c = s */
-    int good = 1;
-    for (int l = 0; l < g->mb && good; ++l) {
-        const int c0 = g->row_first[l];
-        const int d = g->row_first[l + 1] - c0;
-        for (int i = 0; i < Z; ++i) {
-            int par = syn[l * Z + i] & 1;
-            for (int j = 0; j < d; ++j) {
-                const int k = c0 + j;
-                par ^= hard[g->circ_col[k] * Z + (i + g->circ_shift[k]) % Z];
-            }
-            if (par) {
-                good = 0;
-                break;
-            }
+        /* early termination (Discussion, Table tabearly): stop once H c = s */
+        if (cfg->early_every > 0 && (t + 1) % cfg->early_every == 0 && t + 1 < cfg->T &&
+            hard_and_test(g, Lq, syn, hard)) {
+            t_used = t + 1;
+            stopped = 1;
         }
     }
-    *ok = (uint8_t)good;
+
+    /* step 4: hard decision, c_n = 0 iff L_qn >= 0, and the syndrome flag */
+    *ok = (uint8_t)hard_and_test(g, Lq, syn, hard);
+    if (llr_post)
+        for (int i = 0; i < n; ++i) llr_post[i] = Lq[i];
+    if (iters_used) *iters_used = t_used;
     free(Lq); free(Lr); free(q); free(r); free(v); free(ws); free(wo);
     return 0;
 }
@@ -360,6 +374,7 @@ typedef struct {
     uint8_t *hard;
     double *llr_post;
     uint8_t *ok;
+    int32_t *iters_used;
     int tid, nthreads;
     int status;
 } worker_t;
@@ -371,7 +386,8 @@ static void *worker_main(void *arg)
     for (int k = w->tid; k < w->K; k += w->nthreads) {
         int st = decode_frame(w->cfg, w->llr_ch + (size_t)k * w->n, w->syn + (size_t)k * w->m,
                               w->hard + (size_t)k * w->n,
-                              w->llr_post ? w->llr_post + (size_t)k * w->n : NULL, w->ok + k);
+                              w->llr_post ? w->llr_post + (size_t)k * w->n : NULL, w->ok + k,
+                              w->iters_used ? w->iters_used + k : NULL);
         if (st) {
             w->status = st;
             break;
@@ -390,12 +406,16 @@ static void *worker_main(void *arg)
  *   rule         : ORACLE_RULE_*; msg_fmt: ORACLE_MSG_*
  *   w_scale, w_offset : min-sum weights [T][mb][2] (type 0: edge to a variable
  *                  of degree > 1, type 1: edge to a degree-1 variable), or NULL
+ *   early_every  : > 0 tests H c = s after every early_every-th iteration and
+ *                  stops a frame that passes; 0 runs all T iterations
+ *   iters_used   : [K] iterations each frame ran, or NULL
  * Returns 0, or <0 on invalid input / allocation failure.
  */
 int oracle_decode(int mb, int nb, int Z, const int8_t *base, const int32_t *shifts,
                   const int32_t *order, int n_order, int K, int T, const float *llr_ch,
                   const uint8_t *syn, uint8_t *hard, double *llr_post, uint8_t *ok, int rule,
-                  int msg_fmt, const double *w_scale, const double *w_offset, int nthreads)
+                  int msg_fmt, const double *w_scale, const double *w_offset, int nthreads,
+                  int early_every, int32_t *iters_used)
 {
     if (K < 0 || T < 0 || !base || !shifts || (K > 0 && (!llr_ch || !syn || !hard || !ok)))
         return -1;
@@ -420,7 +440,7 @@ int oracle_decode(int mb, int nb, int Z, const int8_t *base, const int32_t *shif
                 return -1;
             }
     }
-    decode_cfg_t cfg = {&g, order, n_order, T, rule, msg_fmt, w_scale, w_offset};
+    decode_cfg_t cfg = {&g, order, n_order, T, rule, msg_fmt, w_scale, w_offset, early_every};
     if (nthreads < 1) nthreads = 1;
     if (nthreads > K) nthreads = K > 0 ? K : 1;
     worker_t *ws = (worker_t *)calloc((size_t)nthreads, sizeof(worker_t));
@@ -431,7 +451,7 @@ int oracle_decode(int mb, int nb, int Z, const int8_t *base, const int32_t *shif
     }
     const int n = nb * Z, m = mb * Z;
     for (int i = 0; i < nthreads; ++i) {
-        ws[i] = (worker_t){&cfg, K, n, m, llr_ch, syn, hard, llr_post, ok, i, nthreads, 0};
+        ws[i] = (worker_t){&cfg, K, n, m, llr_ch, syn, hard, llr_post, ok, iters_used, i, nthreads, 0};
     }
     int started = 0;
     for (int i = 1; i < nthreads; ++i) {

@@ -44,6 +44,7 @@ EXPORTS = (
     "qcmet_code_create", "qcmet_code_create_ex", "qcmet_code_destroy", "qcmet_code_get_info",
     "qcmet_code_get_schedule", "qcmet_decode", "qcmet_decode_ex", "qcmet_decode_host",
     "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
+    "qcmet_decode_early_stop",
 )
 
 
@@ -85,6 +86,8 @@ def _load():
     lib.qcmet_decode_ex.argtypes = dec + [ctypes.POINTER(DecodeOptions), vp]
     lib.qcmet_decode_host.argtypes = dec + [ctypes.POINTER(DecodeOptions), vp]
     lib.qcmet_decode_noalloc.argtypes = dec + [vp]
+    lib.qcmet_decode_early_stop.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp,
+                                            ctypes.POINTER(DecodeOptions), vp]
     lib.qcmet_last_error.argtypes = []
     lib.qcmet_last_error.restype = ctypes.c_char_p
     lib.qcmet_status_string.argtypes = [ctypes.c_int]
@@ -212,6 +215,38 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
                                hard.data_ptr(), llr_post.data_ptr() if llr_post is not None else None,
                                ok.data_ptr(), ctypes.byref(opts), sptr))
     return hard, llr_post, ok
+
+
+def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: int = 1,
+                      msg: str = "fp32", threads: int = 0, stream=None):
+    """Decode with early termination (``qcmet_decode_early_stop``).
+
+    Returns ``(hard, llr_post, ok, iterations_used)`` as CUDA tensors; the call
+    is asynchronous on ``stream``.
+    """
+    import torch
+
+    n = code.base.shape[1] * code.Z
+    m = code.base.shape[0] * code.Z
+    if llr.dtype != torch.float32 or syn.dtype != torch.uint8 or not (llr.is_cuda and syn.is_cuda):
+        raise TypeError("llr must be a float32 CUDA tensor and syn a uint8 CUDA tensor")
+    if llr.dim() != 2 or llr.shape[1] != n or syn.shape != (llr.shape[0], m):
+        raise ValueError(f"expected llr [K, {n}] and syn [K, {m}]")
+    K = llr.shape[0]
+    dev = llr.device
+    hard = torch.empty((K, n), dtype=torch.uint8, device=dev)
+    post = torch.empty((K, n), dtype=torch.float32, device=dev)
+    ok = torch.empty((K,), dtype=torch.uint8, device=dev)
+    iters = torch.empty((K,), dtype=torch.int32, device=dev)
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    opts = _options(msg, threads)
+    _check(lib.qcmet_decode_early_stop(code.handle, llr.data_ptr(), syn.data_ptr(), K,
+                                       int(max_iterations), int(check_every), hard.data_ptr(),
+                                       post.data_ptr(), ok.data_ptr(), iters.data_ptr(),
+                                       ctypes.byref(opts), sptr))
+    return hard, post, ok, iters
 
 
 def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,

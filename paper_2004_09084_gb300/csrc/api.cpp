@@ -96,7 +96,8 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads)
 
 int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                   int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok,
-                  const qcmet_decode_options *opts, void *stream) {
+                  const qcmet_decode_options *opts, void *stream, int32_t check_every = 0,
+                  int32_t *iters_used = nullptr) {
     int32_t fmt, threads;
     int st = check_options(opts, &fmt, &threads);
     if (st) return st;
@@ -142,6 +143,8 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     a.nb = c.nb;
     a.msg_slots = c.msg_slots;
     a.slot_stride = (int64_t)stride;
+    a.check_every = check_every;
+    a.iters_used = iters_used;
     std::string err;
     st = qcmet::launch_decode(a, fmt, threads, stream, err);
     if (st) return fail(st, err);
@@ -235,6 +238,20 @@ int qcmet_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syn
                            stream);
 }
 
+int qcmet_decode_early_stop(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                            int32_t K, int32_t max_iterations, int32_t check_every, uint8_t *hard,
+                            float *llr_post, uint8_t *ok, int32_t *iterations_used,
+                            const qcmet_decode_options *opts, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    if (check_every < 1) return fail(QCMET_ERR_INVALID_ARG, "check_every must be >= 1");
+    if (K > 0 && !iterations_used)
+        return fail(QCMET_ERR_INVALID_ARG, "iterations_used must not be NULL");
+    if (iterations_used && !aligned16(iterations_used))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    return decode_device(const_cast<qcmet_code *>(code)->c, llr_ch, syndrome, K, max_iterations,
+                         hard, llr_post, ok, opts, stream, check_every, iterations_used);
+}
+
 int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
                       int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
                       const qcmet_decode_options *opts, void *stream) {
@@ -315,6 +332,8 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
     a.nb = c.nb;
     a.msg_slots = c.msg_slots;
     a.slot_stride = (int64_t)qcmet::slot_stride(c.Z);
+    a.check_every = 0;
+    a.iters_used = nullptr;
     std::string err;
     int st = qcmet::launch_decode_noalloc(a, c.image.words.data(),
                                           c.image.words.size() * sizeof(int32_t), stream, err);

@@ -398,6 +398,56 @@ __device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a
     }
 }
 
+// Step 4 for frame f: posteriors of the columns that carry no state, hard
+// decisions c_n = [L_qn < 0], and the syndrome test.  Returns, identically in
+// every thread of the block, nonzero when H c != s.
+//   deg1_from_channel: no iteration ran, so degree-1 columns still hold the channel
+template <typename M>
+__device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, const Frame<M> &fr,
+                                       int f, bool deg1_from_channel) {
+    const int Z = s.Z;
+    const size_t n = (size_t)a.n;
+    for (int c = 0; c < s.nb; ++c) {
+        const int kind = s.col_kind[c];
+        const bool from_channel = kind == kColUnconnected || (kind == kColDegree1 && deg1_from_channel);
+        const size_t base = (size_t)c * Z;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+            float L;
+            if (from_channel) {
+                L = fr.ch[base + i];
+                fr.post[base + i] = L;
+            } else {
+                L = fr.post[base + i];
+            }
+            a.hard[(size_t)f * n + base + i] = L < 0.0f ? 1 : 0;
+        }
+    }
+    __syncthreads();
+
+    // Syndrome test: ok = [H c = s].
+    const uint8_t *hard = a.hard + (size_t)f * n;
+    int fail = 0;
+    for (int j = 0; j < s.n_rows; ++j) {
+        const int4 row = s.rows[j];
+        const int4 *ent = s.entries + row.x;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+            unsigned par = fr.syn[row.z + i] & 1u;
+            for (int e = 0; e < row.y; ++e) {
+                const int4 en = ent[e];
+                int jj = i + en.y;
+                jj = jj >= Z ? jj - Z : jj;
+                par ^= hard[en.x + jj];
+            }
+            fail |= (int)par;
+        }
+    }
+    for (int zr = 0; zr < s.n_zero_rows; ++zr) {
+        const size_t cb = (size_t)s.zero_rows[zr] * Z;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x) fail |= fr.syn[cb + i] & 1;
+    }
+    return __syncthreads_or(fail);
+}
+
 template <typename M>
 __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ int4 smem_i4[];
@@ -430,64 +480,41 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
         if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
         __syncthreads();
 
-        // Steps 2-3 over T iterations x layers.
+        // Steps 2-3 over T iterations x layers.  With early termination
+        // (Discussion, Table tabearly) every check_every-th iteration ends with
+        // the hard decision and syndrome test, and a frame that passes stops.
+        // Those iterations, like the last one, also write the posteriors of the
+        // degree-1 columns, which the test needs.
+        int t_stop = T;
+        bool tested = false;
         for (int t = 0; t < T; ++t) {
             const bool first = t == 0;
-            const bool last = t == T - 1;
+            const bool final_iter = t == T - 1;
+            const bool check = final_iter || (a.check_every > 0 && (t + 1) % a.check_every == 0);
             for (int layer = 0; layer < s.n_layers; ++layer) {
                 for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
                     if (threadIdx.x < 32) {
                         if (j + 1 < s.n_rows) prefetch_row<M>(s, a, f, j + 1, t);
-                        else if (!last) prefetch_row<M>(s, a, f, 0, t + 1);
+                        else if (!final_iter) prefetch_row<M>(s, a, f, 0, t + 1);
                     }
                     const int4 row = s.rows[j];
-                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, last);
+                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
                 }
                 __syncthreads();
             }
-        }
-
-        // Step 4: posteriors of stateless columns, hard decisions.
-        for (int c = 0; c < s.nb; ++c) {
-            const int kind = s.col_kind[c];
-            const bool from_channel = kind == kColUnconnected || (kind == kColDegree1 && T == 0);
-            const size_t base = (size_t)c * Z;
-            for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-                float L;
-                if (from_channel) {
-                    L = fr.ch[base + i];
-                    fr.post[base + i] = L;
-                } else {
-                    L = fr.post[base + i];
-                }
-                a.hard[(size_t)f * n + base + i] = L < 0.0f ? 1 : 0;
+            if (a.check_every > 0 && check && !final_iter &&
+                finalize_frame<M>(s, a, fr, f, false) == 0) {
+                t_stop = t + 1;
+                tested = true;
+                break;
             }
         }
-        __syncthreads();
 
-        // Syndrome test: ok = [H c = s].
-        const uint8_t *hard = a.hard + (size_t)f * n;
-        int fail = 0;
-        for (int j = 0; j < s.n_rows; ++j) {
-            const int4 row = s.rows[j];
-            const int4 *ent = s.entries + row.x;
-            for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-                unsigned par = fr.syn[row.z + i] & 1u;
-                for (int e = 0; e < row.y; ++e) {
-                    const int4 en = ent[e];
-                    int jj = i + en.y;
-                    jj = jj >= Z ? jj - Z : jj;
-                    par ^= hard[en.x + jj];
-                }
-                fail |= (int)par;
-            }
+        const int fail = tested ? 0 : finalize_frame<M>(s, a, fr, f, T == 0);
+        if (threadIdx.x == 0) {
+            a.ok[f] = fail ? 0 : 1;
+            if (a.iters_used) a.iters_used[f] = t_stop;
         }
-        for (int zr = 0; zr < s.n_zero_rows; ++zr) {
-            const size_t cb = (size_t)s.zero_rows[zr] * Z;
-            for (int i = threadIdx.x; i < Z; i += blockDim.x) fail |= fr.syn[cb + i] & 1;
-        }
-        fail = __syncthreads_or(fail);
-        if (threadIdx.x == 0) a.ok[f] = fail ? 0 : 1;
         __syncthreads();
     }
 }

@@ -107,6 +107,8 @@ struct DecodeArgs {
     int32_t K, T, Z, n, m, nb;
     int32_t msg_slots;
     int64_t slot_stride;     // elements
+    int32_t check_every;     // > 0: early termination test every check_every iterations
+    int32_t *iters_used;     // [K] iterations each frame ran, or nullptr
 };
 
 // Launch the fused decode kernel for one message format (decode.cu).

@@ -293,6 +293,61 @@ def test_full_size_fixed_iterations_properties(q, full):
 
 
 # --------------------------------------------------------------------------
+# Early termination (Discussion, Table tabearly)
+
+@pytest.fixture(scope="module")
+def converging():
+    code = synth.make_code("0.1", 64)
+    fr = synth.make_frames(code, 24, 0.3)       # most frames decode within a few iterations
+    return code, fr
+
+
+@pytest.mark.parametrize("every", [1, 4])
+def test_early_stop_matches_the_oracle(q, converging, every):
+    code, fr = converging
+    qc = q.Code(code.base, code.shifts, code.Z)
+    h, p, ok, it = q.decode_early_stop(qc, torch.from_numpy(fr.llr).cuda(),
+                                       torch.from_numpy(fr.syn).cuda(), 30, every)
+    torch.cuda.synchronize()
+    h, p, ok, it = h.cpu().numpy(), p.cpu().numpy(), ok.cpu().numpy(), it.cpu().numpy()
+    rh, rp, rok, rit = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 30,
+                                     early_every=every, return_iters=True, nthreads=8)
+    np.testing.assert_array_equal(ok, syndrome_ok(code, h, fr.syn))
+    same = it == rit
+    assert np.mean(same) >= 0.95 and np.any(it < 30)
+    assert rel_err(p[same], rp[same]).max() <= 10 * LLR_TOL
+    assert np.all((it % every == 0) | (it == 30))
+
+
+def test_early_stop_equals_a_fixed_decode_of_that_many_iterations(q, converging):
+    code, fr = converging
+    qc = q.Code(code.base, code.shifts, code.Z)
+    h, p, ok, it = q.decode_early_stop(qc, torch.from_numpy(fr.llr).cuda(),
+                                       torch.from_numpy(fr.syn).cuda(), 25, 2)
+    torch.cuda.synchronize()
+    p, ok, it = p.cpu().numpy(), ok.cpu().numpy(), it.cpu().numpy()
+    for T in sorted(set(it.tolist())):
+        sel = np.flatnonzero(it == T)
+        hh, pp, oo = gpu_decode(q, qc, fr.llr[sel], fr.syn[sel], int(T))
+        np.testing.assert_array_equal(p[sel], pp)
+        np.testing.assert_array_equal(ok[sel], oo)
+        if T < 25:
+            assert np.all(oo == 1)
+
+
+def test_early_stop_arguments(q, small):
+    code, fr = small
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d = torch.zeros((1, code.n), dtype=torch.float32, device="cuda")
+    s = torch.zeros((1, code.m), dtype=torch.uint8, device="cuda")
+    with pytest.raises(q.QcmetError):
+        q.decode_early_stop(qc, d, s, 10, 0)
+    h, p, ok, it = q.decode_early_stop(qc, d[:1] + 1.0, s, 0, 1)   # no iteration: channel decision
+    torch.cuda.synchronize()
+    assert it.item() == 0 and ok.item() == 1
+
+
+# --------------------------------------------------------------------------
 # 16-bit message storage (FP32 arithmetic and posteriors)
 #
 # The oracle rounds every stored message to the same format (IEEE round to

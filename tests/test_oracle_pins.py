@@ -352,3 +352,43 @@ def test_channel_llr_convention():
     fr = synth.make_frames(code, 1, 0.25, noiseless=True)
     # noiseless R = 1 - 2x, sigma^2 = 1/SNR = 4: L = 2R/sigma^2 = +-0.5
     np.testing.assert_allclose(fr.llr[0], 0.5 * (1.0 - 2.0 * fr.x[0]))
+
+
+# --------------------------------------------------------------------------
+# Early termination (Discussion, Table tabearly)
+
+def test_early_termination_stops_at_the_first_passing_check_and_changes_nothing_else():
+    code = synth.make_code("0.1", 16)
+    fr = synth.make_frames(code, 12, 0.3)
+    T = 30
+    for every in (1, 3):
+        h, p, ok, it = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, T,
+                                     early_every=every, return_iters=True)
+        H = helpers.expand_dense(code.base, code.shifts, code.Z)
+        for k in range(12):
+            # a stopped frame equals a fixed-iteration decode of exactly that many iterations
+            hk, pk, okk = oracle.decode(code.base, code.shifts, code.Z, fr.llr[k:k + 1],
+                                        fr.syn[k:k + 1], int(it[k]))
+            np.testing.assert_array_equal(p[k], pk[0])
+            assert ok[k] == okk[0]
+            assert it[k] % every == 0 or it[k] == T
+            # it stopped at the first checked iteration whose hard decision satisfies H c = s
+            for t in range(every, int(it[k]), every):
+                ht, _, okt = oracle.decode(code.base, code.shifts, code.Z, fr.llr[k:k + 1],
+                                           fr.syn[k:k + 1], t)
+                assert okt[0] == 0
+            if it[k] < T:
+                assert ok[k] == 1
+                assert np.all(helpers.syndrome_dense(H, h[k:k + 1])[0] == fr.syn[k])
+        assert np.any(it < T)          # at SNR 0.3 most frames converge early
+
+
+def test_early_termination_off_is_the_fixed_schedule():
+    code = synth.make_code("0.1", 8)
+    fr = synth.make_frames(code, 3, 0.3)
+    a = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 7)
+    b = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 7, early_every=0,
+                      return_iters=True)
+    for u, v in zip(a, b[:3]):
+        np.testing.assert_array_equal(u, v)
+    np.testing.assert_array_equal(b[3], [7, 7, 7])
