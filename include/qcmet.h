@@ -210,6 +210,37 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
                          int32_t K, int32_t iterations, uint8_t *hard, float *llr_post,
                          uint8_t *ok, void *stream);
 
+/*
+ * Learned offset/scaled min-sum (not part of the paper's method; a variant of
+ * its layered decoder, Methods steps 1-4, whose check rule of step 2 becomes)
+ *   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * max(w_scale[t][l][type_e] *
+ *         min_{k != e} |q_k| - w_offset[t][l][type_e], 0)
+ * for iteration t, base row l, and edge type 0 (edge to a variable of degree
+ * > 1) or 1 (edge to a degree-1 variable).  Weights are device FP32 arrays of
+ * shape [iterations][mb][2], row-major.
+ *
+ * qcmet_minsum_decode: decode with given weights; outputs as qcmet_decode
+ *   (FP32 messages, llr_post may be NULL).
+ * qcmet_minsum_forward: training forward.  bits = device [K][n] uint8
+ *   transmitted bits; loss = device [K] FP32 out, per frame the mean over
+ *   iterations t and variables n of softplus(-(1 - 2 x_n) L_qn^(t)), the
+ *   cross-entropy of sigma(-L) against the bits, L^(t) the posterior after
+ *   iteration t.  Keeps what the backward needs in the handle's scratch
+ *   (about K * iterations * (msg_slots + core columns) * Z * 4 bytes); the
+ *   inputs and weights must stay untouched until the backward has run.
+ * qcmet_minsum_backward: gradient of the SUM of the last forward's losses with
+ *   respect to the weights, written to g_scale and g_offset ([iterations][mb][2]
+ *   device FP32, overwritten).  INVALID_ARG without a preceding forward.
+ * All three are stream-ordered; the same handle must not run them concurrently.
+ */
+int qcmet_minsum_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                        int32_t K, int32_t iterations, const float *w_scale, const float *w_offset,
+                        uint8_t *hard, float *llr_post, uint8_t *ok, void *stream);
+int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                         const uint8_t *bits, int32_t K, int32_t iterations, const float *w_scale,
+                         const float *w_offset, float *loss, void *stream);
+int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offset, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qcmet_last_error(void);
 

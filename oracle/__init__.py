@@ -77,6 +77,8 @@ def _load():
     lib.oracle_check_update.restype = None
     lib.oracle_decode.argtypes = [i, i, i, p, p, p, i, i, i, p, p, p, p, p, i, i, p, p, i, i, p]
     lib.oracle_decode.restype = i
+    lib.oracle_minsum_train.argtypes = [i, i, i, p, p, i, i, p, p, p, p, p, p, p, p]
+    lib.oracle_minsum_train.restype = i
     _lib = lib
     return lib
 
@@ -156,3 +158,31 @@ def decode(base, shifts, Z: int, llr, syn, iterations: int, order=None,
     if return_iters:
         return hard, post, ok, iters
     return hard, post, ok
+
+
+def minsum_train(base, shifts, Z: int, llr, syn, x, iterations: int, w_scale, w_offset):
+    """Learned min-sum: per-frame loss and the gradient of the summed loss.
+
+    The loss is the mean over iterations and variables of the cross-entropy
+    of sigma(-L) against the transmitted bits.  Returns ``(loss [K],
+    g_scale [T, mb, 2], g_offset [T, mb, 2])`` in float64.
+    """
+    base = np.ascontiguousarray(base, dtype=np.int8)
+    shifts = np.ascontiguousarray(shifts, dtype=np.int32)
+    mb, nb = base.shape
+    n, m = nb * Z, mb * Z
+    llr = np.ascontiguousarray(llr, dtype=np.float32).reshape(-1, n)
+    syn = np.ascontiguousarray(syn, dtype=np.uint8).reshape(-1, m)
+    x = np.ascontiguousarray(x, dtype=np.uint8).reshape(-1, n)
+    K = llr.shape[0]
+    ws = np.ascontiguousarray(w_scale, dtype=np.float64).reshape(iterations, mb, 2)
+    wo = np.ascontiguousarray(w_offset, dtype=np.float64).reshape(iterations, mb, 2)
+    loss = np.empty((K,), dtype=np.float64)
+    gs = np.empty_like(ws)
+    go = np.empty_like(wo)
+    rc = _load().oracle_minsum_train(mb, nb, int(Z), _ptr(base), _ptr(shifts), K, int(iterations),
+                                     _ptr(llr), _ptr(syn), _ptr(x), _ptr(ws), _ptr(wo),
+                                     _ptr(loss), _ptr(gs), _ptr(go))
+    if rc != 0:
+        raise ValueError(f"oracle_minsum_train failed with status {rc}")
+    return loss, gs, go

@@ -468,3 +468,181 @@ int oracle_decode(int mb, int nb, int Z, const int8_t *base, const int32_t *shif
     free(ws); free(th); free(ord); graph_free(&g);
     return rc;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Learned offset/scaled min-sum: loss and gradient (not part of the      */
+/* paper's method; the training target of the learned variant).           */
+/*                                                                        */
+/* Check rule (for the edge e that receives the message):                  */
+/*   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * max(a_e, 0),               */
+/*   a_e = w_scale[t][l][type_e] * min_{k != e} |q_k| - w_offset[t][l][type_e]
+/* The rest of the layered update is Methods step 3.  Loss: the mean over   */
+/* iterations t and variables n of the binary cross-entropy of the bit     */
+/* estimate sigma(-L_qn^(t)) against the transmitted bit x_n,               */
+/*   loss = 1/(T n) sum_t sum_n softplus(-(1 - 2 x_n) L_qn^(t)),            */
+/* where L^(t) is the posterior after iteration t.  The gradient with      */
+/* respect to the weights comes from reverse-mode differentiation of the   */
+/* unrolled decoder, written out below (adjoints gL of L_qn and gR of the  */
+/* stored L_rmn).                                                          */
+
+static double softplus(double z)
+{
+    return z > 0.0 ? z + log1p(exp(-z)) : log1p(exp(z));
+}
+
+static double sigmoid(double z)
+{
+    return z >= 0.0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
+}
+
+/* Min-sum quantities of one check for the edge j: sign, min over the others,
+ * argmin index among the others. */
+static void minsum_parts(int d, const double *q, int j, double *sign, double *mn, int *arg)
+{
+    double sg = 1.0, m = INFINITY;
+    int a = -1;
+    for (int k = 0; k < d; ++k) {
+        if (k == j) continue;
+        sg *= sgn(q[k]);
+        double v = fabs(q[k]);
+        if (v < m) {
+            m = v;
+            a = k;
+        }
+    }
+    if (d == 1) m = ORACLE_CLIP_MAX;
+    *sign = sg;
+    *mn = m;
+    *arg = a;
+}
+
+static int train_frame(const graph_t *g, int T, const float *llr_ch, const uint8_t *syn,
+                       const uint8_t *x, const double *ws, const double *wo, double *loss,
+                       double *gs, double *go)
+{
+    const int Z = g->Z, mb = g->mb;
+    const int n = g->nb * Z;
+    const size_t E = (size_t)g->n_circ * (size_t)Z;
+    double *Lq = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Lr = (double *)calloc(E ? E : 1, sizeof(double));
+    double *qh = (double *)malloc(sizeof(double) * (E ? E : 1) * (size_t)(T ? T : 1));   /* q per (t, edge) */
+    double *Lh = (double *)malloc(sizeof(double) * (size_t)n * (size_t)(T ? T : 1));     /* L after iteration t */
+    double *gL = (double *)calloc((size_t)n, sizeof(double));
+    double *gR = (double *)calloc(E ? E : 1, sizeof(double));
+    int dmax = g->max_deg > 0 ? g->max_deg : 1;
+    double *q = (double *)malloc(sizeof(double) * dmax), *gr = (double *)malloc(sizeof(double) * dmax);
+    double *gq = (double *)malloc(sizeof(double) * dmax);
+    int *v = (int *)malloc(sizeof(int) * dmax);
+    if (!Lq || !Lr || !qh || !Lh || !gL || !gR || !q || !gr || !gq || !v) {
+        free(Lq); free(Lr); free(qh); free(Lh); free(gL); free(gR); free(q); free(gr); free(gq); free(v);
+        return -2;
+    }
+    for (int i = 0; i < n; ++i) Lq[i] = (double)llr_ch[i];
+    /* forward, recording q and the posteriors after every iteration */
+    double lsum = 0.0;
+    for (int t = 0; t < T; ++t) {
+        for (int l = 0; l < mb; ++l) {
+            const int c0 = g->row_first[l], d = g->row_first[l + 1] - c0;
+            for (int i = 0; i < Z; ++i) {
+                for (int j = 0; j < d; ++j) {
+                    const int k = c0 + j;
+                    v[j] = g->circ_col[k] * Z + (i + g->circ_shift[k]) % Z;
+                    q[j] = Lq[v[j]] - Lr[(size_t)k * Z + i];
+                    qh[(size_t)t * E + (size_t)k * Z + i] = q[j];
+                }
+                const double ssign = (syn[l * Z + i] & 1) ? -1.0 : 1.0;
+                for (int j = 0; j < d; ++j) {
+                    const int k = c0 + j;
+                    double sg, mn;
+                    int arg;
+                    minsum_parts(d, q, j, &sg, &mn, &arg);
+                    const size_t wi = ((size_t)t * mb + l) * 2 + g->circ_type[k];
+                    double a = ws[wi] * mn - wo[wi];
+                    const double r = ssign * sg * (a > 0.0 ? a : 0.0);
+                    Lr[(size_t)k * Z + i] = r;
+                    Lq[v[j]] = q[j] + r;
+                }
+            }
+        }
+        for (int i = 0; i < n; ++i) {
+            Lh[(size_t)t * n + i] = Lq[i];
+            lsum += softplus(-(1.0 - 2.0 * x[i]) * Lq[i]);
+        }
+    }
+    *loss = T > 0 ? lsum / ((double)T * n) : 0.0;
+    /* backward */
+    const double scale = T > 0 ? 1.0 / ((double)T * n) : 0.0;
+    for (int t = T - 1; t >= 0; --t) {
+        /* loss term of the posteriors after iteration t */
+        for (int i = 0; i < n; ++i) {
+            const double sgx = 1.0 - 2.0 * x[i];
+            gL[i] += scale * (-sgx) * sigmoid(-sgx * Lh[(size_t)t * n + i]);
+        }
+        for (int l = mb - 1; l >= 0; --l) {
+            const int c0 = g->row_first[l], d = g->row_first[l + 1] - c0;
+            for (int i = 0; i < Z; ++i) {
+                for (int j = 0; j < d; ++j) {
+                    const int k = c0 + j;
+                    v[j] = g->circ_col[k] * Z + (i + g->circ_shift[k]) % Z;
+                    q[j] = qh[(size_t)t * E + (size_t)k * Z + i];
+                }
+                const double ssign = (syn[l * Z + i] & 1) ? -1.0 : 1.0;
+                /* adjoint of each new message: it enters L_qn and the stored L_rmn */
+                for (int j = 0; j < d; ++j) {
+                    gr[j] = gL[v[j]] + gR[(size_t)(c0 + j) * Z + i];
+                    gq[j] = gL[v[j]];          /* L_qn = q + r */
+                }
+                for (int j = 0; j < d; ++j) {
+                    const int k = c0 + j;
+                    double sg, mn;
+                    int arg;
+                    minsum_parts(d, q, j, &sg, &mn, &arg);
+                    const size_t wi = ((size_t)t * mb + l) * 2 + g->circ_type[k];
+                    const double a = ws[wi] * mn - wo[wi];
+                    if (a <= 0.0) continue;    /* max(a, 0) inactive: no gradient */
+                    const double s = ssign * sg;
+                    gs[wi] += gr[j] * s * mn;
+                    go[wi] += -gr[j] * s;
+                    if (arg >= 0) gq[arg] += gr[j] * s * ws[wi] * sgn(q[arg]);
+                }
+                /* q = L_qn(before) - L_rmn(old) */
+                for (int j = 0; j < d; ++j) {
+                    gL[v[j]] = gq[j];
+                    gR[(size_t)(c0 + j) * Z + i] = -gq[j];
+                }
+            }
+        }
+    }
+    free(Lq); free(Lr); free(qh); free(Lh); free(gL); free(gR); free(q); free(gr); free(gq); free(v);
+    return 0;
+}
+
+/*
+ * Learned min-sum training quantities for K frames (base-row order):
+ *   x          : [K][n] transmitted bits
+ *   w_scale, w_offset : [T][mb][2] weights (type 0: edge to a variable of
+ *                degree > 1, type 1: edge to a degree-1 variable)
+ *   loss       : [K] out, per-frame loss
+ *   g_scale, g_offset : [T][mb][2] out, gradient of the SUM of the K losses
+ * Returns 0, or <0 on invalid input / allocation failure.
+ */
+int oracle_minsum_train(int mb, int nb, int Z, const int8_t *base, const int32_t *shifts, int K,
+                        int T, const float *llr_ch, const uint8_t *syn, const uint8_t *x,
+                        const double *w_scale, const double *w_offset, double *loss,
+                        double *g_scale, double *g_offset)
+{
+    if (K < 0 || T < 0 || !base || !shifts || !w_scale || !w_offset || !g_scale || !g_offset)
+        return -1;
+    graph_t g;
+    int st = graph_build(mb, nb, Z, base, shifts, &g);
+    if (st) return st;
+    const size_t nw = (size_t)T * mb * 2;
+    for (size_t i = 0; i < nw; ++i) g_scale[i] = g_offset[i] = 0.0;
+    const int n = nb * Z, m = mb * Z;
+    int rc = 0;
+    for (int k = 0; k < K && !rc; ++k)
+        rc = train_frame(&g, T, llr_ch + (size_t)k * n, syn + (size_t)k * m, x + (size_t)k * n,
+                         w_scale, w_offset, loss + k, g_scale, g_offset);
+    graph_free(&g);
+    return rc;
+}

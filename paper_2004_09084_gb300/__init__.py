@@ -44,7 +44,8 @@ EXPORTS = (
     "qcmet_code_create", "qcmet_code_create_ex", "qcmet_code_destroy", "qcmet_code_get_info",
     "qcmet_code_get_schedule", "qcmet_decode", "qcmet_decode_ex", "qcmet_decode_host",
     "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
-    "qcmet_decode_early_stop",
+    "qcmet_decode_early_stop", "qcmet_minsum_decode", "qcmet_minsum_forward",
+    "qcmet_minsum_backward",
 )
 
 
@@ -88,6 +89,9 @@ def _load():
     lib.qcmet_decode_noalloc.argtypes = dec + [vp]
     lib.qcmet_decode_early_stop.argtypes = [vp, vp, vp, i32, i32, i32, vp, vp, vp, vp,
                                             ctypes.POINTER(DecodeOptions), vp]
+    lib.qcmet_minsum_decode.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.qcmet_minsum_forward.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
+    lib.qcmet_minsum_backward.argtypes = [vp, vp, vp, vp]
     lib.qcmet_last_error.argtypes = []
     lib.qcmet_last_error.restype = ctypes.c_char_p
     lib.qcmet_status_string.argtypes = [ctypes.c_int]

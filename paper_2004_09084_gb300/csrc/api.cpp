@@ -191,6 +191,7 @@ void qcmet_code_destroy(qcmet_code *code) {
     if (c.d_msgs) cudaFree(c.d_msgs);
     if (c.d_post) cudaFree(c.d_post);
     if (c.d_io) cudaFree(c.d_io);
+    if (c.d_learned) cudaFree(c.d_learned);
     delete code;
 }
 
@@ -337,6 +338,147 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
     std::string err;
     int st = qcmet::launch_decode_noalloc(a, c.image.words.data(),
                                           c.image.words.size() * sizeof(int32_t), stream, err);
+    if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
+// ---- learned offset/scaled min-sum ----------------------------------------
+
+namespace {
+
+size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// base columns of degree > 1 (those whose posteriors are decoder state)
+size_t core_cols_of(const qcmet::Code &c) {
+    size_t k = 0;
+    for (int32_t d : c.col_degree) k += d > 1;
+    return k;
+}
+
+// Fill the code-dependent fields and carve the learned scratch for K frames and
+// T iterations (training adds q and posterior histories and the adjoints).
+int learned_setup(qcmet::Code &c, int32_t K, int32_t T, bool train, bool need_post,
+                  qcmet::LearnedArgs &a) {
+    int st = ensure_device(c);
+    if (st) return st;
+    const size_t n = (size_t)c.nb * c.Z, stride = qcmet::slot_stride(c.Z);
+    const size_t msgs = r256((size_t)K * c.msg_slots * stride * sizeof(float));
+    const size_t post = need_post ? r256((size_t)K * n * sizeof(float)) : 0;
+    const size_t core_vars = core_cols_of(c) * (size_t)c.Z;
+    const size_t qhist = train ? r256((size_t)K * T * c.msg_slots * stride * sizeof(float)) : 0;
+    const size_t lhist = train ? r256((size_t)K * T * core_vars * sizeof(float)) : 0;
+    const size_t gl = train ? r256((size_t)K * core_vars * sizeof(float)) : 0;
+    const size_t gr = train ? r256((size_t)K * c.msg_slots * stride * sizeof(float)) : 0;
+    const size_t total = msgs + post + qhist + lhist + gl + gr + 256;
+    st = grow(&c.d_learned, &c.learned_bytes, total, "cudaMalloc(learned scratch)");
+    if (st) return st;
+    char *p = static_cast<char *>(c.d_learned);
+    a = qcmet::LearnedArgs{};
+    a.msgs = reinterpret_cast<float *>(p);
+    p += msgs;
+    a.post = need_post ? reinterpret_cast<float *>(p) : nullptr;
+    p += post;
+    a.qhist = train ? reinterpret_cast<float *>(p) : nullptr;
+    p += qhist;
+    a.Lhist = train ? reinterpret_cast<float *>(p) : nullptr;
+    p += lhist;
+    a.gL = train ? reinterpret_cast<float *>(p) : nullptr;
+    p += gl;
+    a.gR = train ? reinterpret_cast<float *>(p) : nullptr;
+    a.image = c.d_image;
+    a.image_words = (int32_t)c.image.words.size();
+    a.K = K;
+    a.T = T;
+    a.Z = c.Z;
+    a.n = (int32_t)n;
+    a.m = c.mb * c.Z;
+    a.nb = c.nb;
+    a.mb = c.mb;
+    a.msg_slots = c.msg_slots;
+    a.slot_stride = (int64_t)stride;
+    return QCMET_OK;
+}
+
+}  // namespace
+
+int qcmet_minsum_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                        int32_t K, int32_t iterations, const float *w_scale, const float *w_offset,
+                        uint8_t *hard, float *llr_post, uint8_t *ok, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    if (K < 0 || iterations < 0) return fail(QCMET_ERR_INVALID_ARG, "K and iterations must be >= 0");
+    if (K == 0) return QCMET_OK;
+    if (!llr_ch || !syndrome || !hard || !ok || (iterations > 0 && (!w_scale || !w_offset)))
+        return fail(QCMET_ERR_INVALID_ARG, "llr_ch, syndrome, w_scale, w_offset, hard and ok must not be NULL");
+    if (!aligned16(llr_ch) || !aligned16(syndrome) || !aligned16(hard) || !aligned16(ok) ||
+        (llr_post && !aligned16(llr_post)) || (w_scale && !aligned16(w_scale)) ||
+        (w_offset && !aligned16(w_offset)))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    qcmet::Code &c = const_cast<qcmet_code *>(code)->c;
+    qcmet::LearnedArgs a;
+    int st = learned_setup(c, K, iterations, false, llr_post == nullptr, a);
+    if (st) return st;
+    if (llr_post) a.post = llr_post;
+    a.ch = llr_ch;
+    a.syn = syndrome;
+    a.w_scale = w_scale;
+    a.w_offset = w_offset;
+    a.hard = hard;
+    a.ok = ok;
+    std::string err;
+    st = qcmet::launch_learned_forward(a, false, stream, err);
+    if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
+int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
+                         const uint8_t *bits, int32_t K, int32_t iterations, const float *w_scale,
+                         const float *w_offset, float *loss, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    if (K < 0 || iterations < 0) return fail(QCMET_ERR_INVALID_ARG, "K and iterations must be >= 0");
+    qcmet::Code &c = const_cast<qcmet_code *>(code)->c;
+    c.learned_ready = false;
+    if (K == 0) return QCMET_OK;
+    if (!llr_ch || !syndrome || !bits || !loss || (iterations > 0 && (!w_scale || !w_offset)))
+        return fail(QCMET_ERR_INVALID_ARG, "llr_ch, syndrome, bits, w_scale, w_offset and loss must not be NULL");
+    if (!aligned16(llr_ch) || !aligned16(syndrome) || !aligned16(bits) || !aligned16(loss) ||
+        (w_scale && !aligned16(w_scale)) || (w_offset && !aligned16(w_offset)))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    qcmet::LearnedArgs a;
+    int st = learned_setup(c, K, iterations, true, true, a);
+    if (st) return st;
+    a.ch = llr_ch;
+    a.syn = syndrome;
+    a.x = bits;
+    a.w_scale = w_scale;
+    a.w_offset = w_offset;
+    a.loss = loss;
+    std::string err;
+    st = qcmet::launch_learned_forward(a, true, stream, err);
+    if (st) return fail(st, err);
+    c.learned_last = a;
+    c.learned_ready = true;
+    return QCMET_OK;
+}
+
+int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offset, void *stream) {
+    if (!code) return fail(QCMET_ERR_INVALID_ARG, "code must not be NULL");
+    qcmet::Code &c = const_cast<qcmet_code *>(code)->c;
+    if (!c.learned_ready)
+        return fail(QCMET_ERR_INVALID_ARG, "qcmet_minsum_backward needs a preceding qcmet_minsum_forward on this handle");
+    if (!g_scale || !g_offset) return fail(QCMET_ERR_INVALID_ARG, "g_scale and g_offset must not be NULL");
+    if (!aligned16(g_scale) || !aligned16(g_offset))
+        return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
+    qcmet::LearnedArgs a = c.learned_last;
+    const size_t nw = (size_t)a.T * c.mb * 2 * sizeof(float);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(g_scale, 0, nw, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_offset, 0, nw, s);
+    if (e != cudaSuccess) return cuda_fail("cudaMemsetAsync(gradients)", e);
+    if (a.T == 0) return QCMET_OK;
+    a.g_scale = g_scale;
+    a.g_offset = g_offset;
+    std::string err;
+    int st = qcmet::launch_learned_backward(a, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
 }

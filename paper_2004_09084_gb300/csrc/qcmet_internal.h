@@ -58,6 +58,30 @@ struct ScheduleImage {
     int32_t n_zero_rows = 0;
 };
 
+// Arguments of the learned min-sum kernels (learned.cu).
+struct LearnedArgs {
+    const float *ch;          // [K][n]
+    const uint8_t *syn;       // [K][m]
+    const uint8_t *x;         // [K][n] transmitted bits (training)
+    float *post;              // [K][n] posteriors
+    float *msgs;              // [K][slots][stride] messages (FP32)
+    const float *w_scale;     // [T][mb][2]
+    const float *w_offset;    // [T][mb][2]
+    float *qhist;             // [K][T][slots][stride] q of core edges (training)
+    float *Lhist;             // [K][T][core_cols*Z] core posteriors after each iteration (training)
+    float *loss;              // [K] (training)
+    float *g_scale;           // [T][mb][2] (backward, accumulated)
+    float *g_offset;          // [T][mb][2] (backward, accumulated)
+    float *gL;                // [K][core_cols*Z] adjoint of the core posteriors (backward)
+    float *gR;                // [K][slots][stride] adjoint of the stored messages (backward)
+    uint8_t *hard;            // [K][n] (inference)
+    uint8_t *ok;              // [K] (inference)
+    const int32_t *image;
+    int32_t image_words;
+    int32_t K, T, Z, n, m, nb, mb, msg_slots;
+    int64_t slot_stride;
+};
+
 struct Code {
     int32_t mb = 0, nb = 0, Z = 0;
     int32_t merge_mode = QCMET_MERGE_EXACT;
@@ -84,6 +108,11 @@ struct Code {
     // staging buffers of qcmet_decode_host
     void *d_io = nullptr;
     size_t io_bytes = 0;
+    // learned min-sum: scratch and the arguments of the last training forward
+    void *d_learned = nullptr;
+    size_t learned_bytes = 0;
+    bool learned_ready = false;
+    LearnedArgs learned_last{};
 };
 
 // Host builder (layout.cpp).  Returns a QCMET status; fills `err` on failure.
@@ -110,6 +139,9 @@ struct DecodeArgs {
     int32_t check_every;     // > 0: early termination test every check_every iterations
     int32_t *iters_used;     // [K] iterations each frame ran, or nullptr
 };
+
+int launch_learned_forward(const LearnedArgs &a, bool train, void *stream, std::string &err);
+int launch_learned_backward(const LearnedArgs &a, void *stream, std::string &err);
 
 // Launch the fused decode kernel for one message format (decode.cu).
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,

@@ -392,3 +392,48 @@ def test_early_termination_off_is_the_fixed_schedule():
     for u, v in zip(a, b[:3]):
         np.testing.assert_array_equal(u, v)
     np.testing.assert_array_equal(b[3], [7, 7, 7])
+
+
+# --------------------------------------------------------------------------
+# Learned min-sum: loss and its gradient (the training target of the learned variant)
+
+def _minsum_case(Z=4, K=2, T=3, seed=0, snr=0.3):
+    code = synth.make_code("0.1", Z)
+    fr = synth.make_frames(code, K, snr)
+    rng = np.random.default_rng(seed)
+    ws = 0.7 + 0.3 * rng.random((T, code.mb, 2))
+    wo = 0.3 * rng.random((T, code.mb, 2))
+    return code, fr, T, ws, wo
+
+
+def test_minsum_gradient_matches_central_differences():
+    code, fr, T, ws, wo = _minsum_case()
+    loss, gs, go = oracle.minsum_train(code.base, code.shifts, code.Z, fr.llr, fr.syn, fr.x, T,
+                                       ws, wo)
+    rng = np.random.default_rng(1)
+    eps = 1e-6
+    picks = [tuple(rng.integers(0, s) for s in ws.shape) for _ in range(12)]
+    picks += [(0, 0, 0), (T - 1, 1, 0), (1, 5, 1)]
+    for idx in picks:
+        for which in ("scale", "offset"):
+            def f(delta):
+                a, b = ws.copy(), wo.copy()
+                (a if which == "scale" else b)[idx] += delta
+                return oracle.minsum_train(code.base, code.shifts, code.Z, fr.llr, fr.syn, fr.x,
+                                           T, a, b)[0].sum()
+            fd = (f(eps) - f(-eps)) / (2 * eps)
+            an = (gs if which == "scale" else go)[idx]
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (which, idx)
+
+
+def test_minsum_loss_is_the_mean_cross_entropy_of_the_decoder_posteriors():
+    code, fr, T, ws, wo = _minsum_case(T=2)
+    loss, _, _ = oracle.minsum_train(code.base, code.shifts, code.Z, fr.llr, fr.syn, fr.x, T,
+                                     ws, wo)
+    sgx = 1.0 - 2.0 * fr.x.astype(np.float64)
+    terms = []
+    for t in (1, 2):
+        _, post, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, t,
+                                   rule=oracle.RULE_MINSUM, w_scale=ws, w_offset=wo)
+        terms.append(np.logaddexp(0.0, -sgx * post).mean(axis=1))
+    np.testing.assert_allclose(loss, np.mean(terms, axis=0), rtol=1e-12)
