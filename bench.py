@@ -434,6 +434,87 @@ def run_report(args):
                                            "hard_agree": float(np.mean((p5 < 0) == (rp[0] < 0)))},
                 }), flush=True)
         return 0
+    if args.report == "learned":
+        # learned offset/scaled min-sum: train on decoder-generated frames, then
+        # compare with plain min-sum and tanh-rule BP on held-out frames
+        from paper_2004_09084_gb300 import learned
+        code = synth.make_code(RATE, Z)
+        qc = q.Code(code.base, code.shifts, code.Z)
+        T = 30
+        frames, batch = args.train_frames, 16
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2004)
+        ws, wo = learned.init_weights(qc, T, device=dev)
+        ws.requires_grad_()
+        wo.requires_grad_()
+        opt = torch.optim.Adam([ws, wo], lr=0.01)
+        t0 = time.perf_counter()
+        losses = []
+        for step in range(max(1, frames // batch)):
+            llr, syn, x = learned.make_batch(qc, batch, 0.15, 0.17, gen)
+            opt.zero_grad()
+            loss = learned.minsum_loss(ws, wo, qc, llr, syn, x).mean()
+            loss.backward()
+            opt.step()
+            with torch.no_grad():
+                ws.clamp_(0.0, 2.0)
+                wo.clamp_(0.0, 5.0)
+            losses.append(float(loss.item()))
+        torch.cuda.synchronize(dev)
+        train_s = time.perf_counter() - t0
+        print(json.dumps({"report": "learned-training", "frames": frames, "batch": batch,
+                          "iterations": T, "snr_range": [0.15, 0.17], "seconds": train_s,
+                          "loss_first": losses[0], "loss_last10": float(np.mean(losses[-10:]))}),
+              flush=True)
+        plain_s, plain_o = learned.init_weights(qc, T, device=dev)
+        for snr in (0.161, 0.2, 0.22):
+            gen.manual_seed(777)
+            llr, syn, x = learned.make_batch(qc, K_FRAMES, snr, snr, gen)
+            res = {}
+            for name, fn in (("bp", lambda: q.decode(qc, llr, syn, T)),
+                             ("minsum", lambda: learned.decode(qc, llr, syn, plain_s, plain_o)),
+                             ("learned", lambda: learned.decode(qc, llr, syn, ws, wo))):
+                ms, (h, _, ok) = timed(fn)
+                res[name] = {"ms": ms, "mbit_s": K_FRAMES * code.n / ms / 1e3,
+                             "fer": float((h != x).any(dim=1).float().mean().item()),
+                             "ber": float((h != x).float().mean().item()),
+                             "ok_rate": float(ok.float().mean().item())}
+            print(json.dumps({"report": "learned", "snr": snr, "iterations": T, **res}), flush=True)
+        if args.save_weights:
+            np.savez(args.save_weights, w_scale=ws.detach().cpu().numpy(),
+                     w_offset=wo.detach().cpu().numpy())
+        return 0
+    if args.report == "batch":
+        # configs[4]: 192 codewords across rates 0.1/0.05/0.02 and lengths
+        # 1e5 / 5e5 / 1e6 (Z = 1250 / 6250 / 12500) in one graph-captured launch
+        plan = [(Zl, Kl) for Zl, Kl in ((1250, 22), (6250, 21), (12500, 21))]
+        frames, bits, groups = [], 0, []
+        for rate in ("0.1", "0.05", "0.02"):
+            for j, (Zl, Kl) in enumerate(plan):
+                code = synth.make_code(rate, Zl)
+                qc = q.Code(code.base, code.shifts, code.Z)
+                fr = synth.make_frames(code, Kl, synth.RATE_SNR[rate], first=70_000 + 100 * j)
+                llr = torch.from_numpy(fr.llr).to(dev)
+                syn = torch.from_numpy(fr.syn).to(dev)
+                groups.append((qc, llr, syn))
+                for k in range(Kl):   # one allocation per frame keeps every row 16-byte aligned
+                    frames.append((qc, llr[k].clone(), syn[k].clone()))
+                bits += Kl * code.n
+        T = ITERS
+        for msg in ("fp16", "fp32"):
+            t0 = time.perf_counter()
+            b = q.Batch(frames, T, msg=msg, autotune=True)
+            create_s = time.perf_counter() - t0
+            ms, _ = timed(lambda: b.run())
+            # the same frames as one launch per (rate, length) group
+            ms_sep, _ = timed(lambda: [q.decode(qc, llr, syn, T, msg=msg) for qc, llr, syn in groups])
+            print(json.dumps({"report": "batch", "frames": len(frames), "bits": bits, "msg": msg,
+                              "iterations": T, "ms": ms, "mbit_s": bits / ms / 1e3,
+                              "separate_launches_ms": ms_sep,
+                              "separate_launches_mbit_s": bits / ms_sep / 1e3,
+                              "create_s": create_s, "config": b.config()}), flush=True)
+            b.close()
+        return 0
     raise SystemExit(f"unknown report {args.report}")
 
 
@@ -450,7 +531,10 @@ def main():
     ap.add_argument("--frames", type=int, default=K_FRAMES)
     ap.add_argument("--iters", type=int, default=ITERS)
     ap.add_argument("--launches", type=int, default=2)
-    ap.add_argument("--report", choices=["early-stop", "precision"],
+    ap.add_argument("--train-frames", type=int, default=10_000,
+                    help="--report learned: training frames (decoder-generated)")
+    ap.add_argument("--save-weights", default="", help="--report learned: write weights (.npz)")
+    ap.add_argument("--report", choices=["early-stop", "precision", "learned", "batch"],
                     help="print secondary measurements instead of the bench line")
     args = ap.parse_args()
     if args.report:

@@ -241,6 +241,56 @@ int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint
                          const float *w_offset, float *loss, void *stream);
 int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offset, void *stream);
 
+/*
+ * Mixed batches: frames of different codes (rates, lengths) decoded by ONE
+ * launch of the layered decoder, so that short and long codewords share the
+ * GPU (the paper decodes many codewords of one code at once, Results,
+ * multi-codeword decoding; mixing codes is this library's extension).
+ *
+ * A batch is a plan over fixed buffers: qcmet_batch_create records the frames,
+ * allocates the messages (and posteriors where llr_post is NULL), chooses a
+ * launch configuration and captures the launch in a CUDA graph;
+ * qcmet_batch_run replays that graph on `stream` (asynchronous).  To decode
+ * new data, write it into the same input buffers and run again.
+ *
+ * Autotuning (autotune != 0) times, on this batch with min(iterations, 4)
+ * iterations, every combination of block size (512, 1024), layer schedule
+ * (each code's own, or the other schedule that gives identical results:
+ * base-row order <-> merged rows, Results Eqs. (m1), (m2)) and frame order
+ * (largest first, or as given), and keeps the fastest.  All candidates give
+ * the same results, so the choice affects time only.  Autotuning runs trial
+ * decodes, so the inputs must be valid and the outputs writable at creation.
+ * Frames are taken by persistent thread blocks from a work counter.
+ */
+typedef struct {
+    const qcmet_code *code;   /* the frame's code                          */
+    const float *llr_ch;      /* device [n] channel LLRs                   */
+    const uint8_t *syndrome;  /* device [m] syndrome bits                  */
+    uint8_t *hard;            /* device [n] out                            */
+    float *llr_post;          /* device [n] out, or NULL                   */
+    uint8_t *ok;              /* device [1] out, 1 iff H*hard = syndrome   */
+} qcmet_frame;
+
+typedef struct qcmet_batch qcmet_batch;
+
+typedef struct {
+    int32_t threads_per_block;   /* chosen block size                                  */
+    int32_t alternate_schedule;  /* 1: the codes' other exact schedule was faster       */
+    int32_t largest_first;       /* 1: frames are taken in decreasing edge count       */
+    int32_t candidates;          /* configurations timed (1 without autotuning)        */
+    float trial_ms;              /* time of two trial decodes of the winner (-1 if none) */
+    int32_t reserved[3];
+} qcmet_batch_config;
+
+/* frames: host array [K] (copied); msg_format: QCMET_MSG_*.  Pointers must be
+ * 16-byte aligned.  Errors: INVALID_ARG, ALIGNMENT, OOM, CUDA. */
+int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
+                       int32_t msg_format, int32_t autotune, void *stream, qcmet_batch **out);
+int qcmet_batch_run(qcmet_batch *batch, void *stream);
+int qcmet_batch_get_config(const qcmet_batch *batch, qcmet_batch_config *out);
+/* Frees the plan (not the codes or the caller's buffers).  NULL is a no-op. */
+void qcmet_batch_destroy(qcmet_batch *batch);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *qcmet_last_error(void);
 

@@ -45,7 +45,8 @@ EXPORTS = (
     "qcmet_code_get_schedule", "qcmet_decode", "qcmet_decode_ex", "qcmet_decode_host",
     "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
     "qcmet_decode_early_stop", "qcmet_minsum_decode", "qcmet_minsum_forward",
-    "qcmet_minsum_backward",
+    "qcmet_minsum_backward", "qcmet_batch_create", "qcmet_batch_run", "qcmet_batch_get_config",
+    "qcmet_batch_destroy",
 )
 
 
@@ -61,6 +62,18 @@ class CodeInfo(ctypes.Structure):
                 ("circulants", ctypes.c_int32), ("msg_slots", ctypes.c_int32),
                 ("degree1_columns", ctypes.c_int32), ("layers", ctypes.c_int32),
                 ("max_row_degree", ctypes.c_int32), ("merge_mode", ctypes.c_int32)]
+
+
+class Frame(ctypes.Structure):
+    _fields_ = [("code", ctypes.c_void_p), ("llr_ch", ctypes.c_void_p),
+                ("syndrome", ctypes.c_void_p), ("hard", ctypes.c_void_p),
+                ("llr_post", ctypes.c_void_p), ("ok", ctypes.c_void_p)]
+
+
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("alternate_schedule", ctypes.c_int32),
+                ("largest_first", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("trial_ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
 
 
 class DecodeOptions(ctypes.Structure):
@@ -80,6 +93,7 @@ def _load():
     lib.qcmet_code_create_ex.argtypes = [vp, vp, i32, i32, i32, i32, ctypes.POINTER(vp)]
     lib.qcmet_code_destroy.argtypes = [vp]
     lib.qcmet_code_destroy.restype = None
+    lib.qcmet_batch_destroy.restype = None
     lib.qcmet_code_get_info.argtypes = [vp, ctypes.POINTER(CodeInfo)]
     lib.qcmet_code_get_schedule.argtypes = [vp, vp, vp]
     dec = [vp, vp, vp, i32, i32, vp, vp, vp]
@@ -92,13 +106,19 @@ def _load():
     lib.qcmet_minsum_decode.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
     lib.qcmet_minsum_forward.argtypes = [vp, vp, vp, vp, i32, i32, vp, vp, vp, vp]
     lib.qcmet_minsum_backward.argtypes = [vp, vp, vp, vp]
+    lib.qcmet_batch_create.argtypes = [ctypes.POINTER(Frame), i32, i32, i32, i32, vp,
+                                       ctypes.POINTER(vp)]
+    lib.qcmet_batch_run.argtypes = [vp, vp]
+    lib.qcmet_batch_get_config.argtypes = [vp, ctypes.POINTER(BatchConfig)]
+    lib.qcmet_batch_destroy.argtypes = [vp]
     lib.qcmet_last_error.argtypes = []
     lib.qcmet_last_error.restype = ctypes.c_char_p
     lib.qcmet_status_string.argtypes = [ctypes.c_int]
     lib.qcmet_status_string.restype = ctypes.c_char_p
     lib.qcmet_version.argtypes = []
     for name in EXPORTS:
-        if name not in ("qcmet_code_destroy", "qcmet_last_error", "qcmet_status_string"):
+        if name not in ("qcmet_code_destroy", "qcmet_last_error", "qcmet_status_string",
+                        "qcmet_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     del i64
     return lib
@@ -280,3 +300,62 @@ def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
                                  post.ctypes.data if post is not None else None, ok.ctypes.data,
                                  ctypes.byref(opts), sptr))
     return hard, post, ok
+
+
+class Batch:
+    """A mixed batch plan (``qcmet_batch_*``): frames of several codes, one launch.
+
+    ``frames`` is a list of ``(code, llr, syn)`` with CUDA tensors of that
+    code's sizes.  Outputs are allocated here (``self.hard``, ``self.post``,
+    ``self.ok``); :meth:`run` replays the captured graph.  Keep the input
+    tensors alive and write new data into them to decode again.
+    """
+
+    def __init__(self, frames, iterations: int, msg: str = "fp32", autotune: bool = True,
+                 stream=None, want_post: bool = True):
+        import torch
+        self._keep = []
+        arr = (Frame * len(frames))()
+        self.hard, self.post, self.ok = [], [], []
+        for k, (code, llr, syn) in enumerate(frames):
+            n = code.base.shape[1] * code.Z
+            m = code.base.shape[0] * code.Z
+            if llr.numel() != n or syn.numel() != m or llr.dtype != torch.float32 \
+                    or syn.dtype != torch.uint8 or not (llr.is_cuda and syn.is_cuda):
+                raise ValueError(f"frame {k}: expected float32 llr [{n}] and uint8 syn [{m}] on CUDA")
+            h = torch.empty((n,), dtype=torch.uint8, device=llr.device)
+            o = torch.empty((16,), dtype=torch.uint8, device=llr.device)
+            p = torch.empty((n,), dtype=torch.float32, device=llr.device) if want_post else None
+            self.hard.append(h)
+            self.ok.append(o)
+            self.post.append(p)
+            self._keep += [code, llr, syn]
+            arr[k] = Frame(code.handle.value, llr.data_ptr(), syn.data_ptr(), h.data_ptr(),
+                           p.data_ptr() if p is not None else None, o.data_ptr())
+        self._h = ctypes.c_void_p()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check(lib.qcmet_batch_create(arr, len(frames), int(iterations), MSG[msg],
+                                      1 if autotune else 0, self._stream, ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        s = self._stream if stream is None else (
+            stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(lib.qcmet_batch_run(self._h, s))
+
+    def config(self) -> dict:
+        c = BatchConfig()
+        _check(lib.qcmet_batch_get_config(self._h, ctypes.byref(c)))
+        return {name: getattr(c, name) for name, _ in BatchConfig._fields_ if name != "reserved"}
+
+    def close(self):
+        if self._h:
+            lib.qcmet_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -23,7 +23,7 @@ BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libqcmet_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["layout.cpp", "api.cpp", "decode.cu", "learned.cu"]
+SOURCES = ["layout.cpp", "api.cpp", "batch.cpp", "decode.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           f"-I{INCLUDE}"]

@@ -10,10 +10,6 @@
 
 #include "qcmet_internal.h"
 
-struct qcmet_code {
-    qcmet::Code c;
-};
-
 namespace {
 
 thread_local std::string g_last_error;
@@ -154,6 +150,11 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
+
+namespace qcmet {
+int ensure_device_image(Code &c) { return ensure_device(c); }
+int set_error(int status, const std::string &msg) { return fail(status, msg); }
+}  // namespace qcmet
 
 extern "C" {
 

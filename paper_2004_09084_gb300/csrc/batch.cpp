@@ -1,0 +1,290 @@
+// Mixed batches: frames of several codes decoded by one launch of the batch
+// kernel (decode.cu), captured once into a CUDA graph and replayed.  The plan
+// picks its launch configuration by timing candidates on the batch itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qcmet_internal.h"
+
+struct qcmet_batch {
+    std::vector<qcmet_frame> frames;
+    int32_t K = 0, T = 0, fmt = QCMET_MSG_FP32;
+    std::vector<const qcmet_code *> codes;          // distinct codes, by first appearance
+    std::vector<int32_t> frame_code;                // [K] index into codes
+    std::vector<qcmet_code *> alt;                  // same codes with the other exact schedule
+    qcmet_batch_config cfg{};
+    int32_t max_image_words = 0;
+    void *d_scratch = nullptr;                      // messages (+ posteriors), descriptors, order, counter
+    qcmet::BatchFrame *d_frames = nullptr;
+    int32_t *d_order = nullptr;
+    int32_t *d_counter = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
+size_t msg_size(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 4 : 2; }
+
+int cuda_err(const char *what, cudaError_t e) {
+    return qcmet::set_error(e == cudaErrorMemoryAllocation ? QCMET_ERR_OOM : QCMET_ERR_CUDA,
+                            std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Descriptors for one configuration: which schedule variant and which order.
+int write_descriptors(qcmet_batch &b, bool alt, bool largest_first, cudaStream_t s) {
+    std::vector<qcmet::BatchFrame> fd(b.K);
+    char *p = static_cast<char *>(b.d_scratch);
+    size_t off = 0;
+    b.max_image_words = 0;
+    for (int32_t k = 0; k < b.K; ++k) {
+        const qcmet_code *h = alt && b.alt[b.frame_code[k]] ? b.alt[b.frame_code[k]]
+                                                            : b.codes[b.frame_code[k]];
+        qcmet::Code &c = const_cast<qcmet_code *>(h)->c;
+        int st = qcmet::ensure_device_image(c);
+        if (st) return st;
+        const qcmet_frame &f = b.frames[k];
+        qcmet::BatchFrame &d = fd[k];
+        d.image = c.d_image;
+        d.image_words = (int32_t)c.image.words.size();
+        d.code_id = b.frame_code[k];
+        d.ch = f.llr_ch;
+        d.syn = f.syndrome;
+        d.hard = f.hard;
+        d.ok = f.ok;
+        d.Z = c.Z;
+        d.n = c.nb * c.Z;
+        d.m = c.mb * c.Z;
+        d.nb = c.nb;
+        d.msg_slots = c.msg_slots;
+        d.slot_stride = (int64_t)qcmet::slot_stride(c.Z);
+        d.msgs = p + off;
+        off += r256((size_t)c.msg_slots * (size_t)d.slot_stride * msg_size(b.fmt));
+        if (f.llr_post) {
+            d.post = f.llr_post;
+        } else {
+            d.post = reinterpret_cast<float *>(p + off);
+            off += r256((size_t)d.n * sizeof(float));
+        }
+        b.max_image_words = std::max(b.max_image_words, d.image_words);
+    }
+    std::vector<int32_t> order(b.K);
+    for (int32_t k = 0; k < b.K; ++k) order[k] = k;
+    if (largest_first) {
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            const qcmet::Code &cx = b.codes[b.frame_code[x]]->c, &cy = b.codes[b.frame_code[y]]->c;
+            return (int64_t)cx.circulants * cx.Z > (int64_t)cy.circulants * cy.Z;
+        });
+    }
+    cudaError_t e = cudaMemcpyAsync(b.d_frames, fd.data(), fd.size() * sizeof(qcmet::BatchFrame),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b.d_order, order.data(), order.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors go out of scope
+    if (e != cudaSuccess) return cuda_err("cudaMemcpyAsync(batch descriptors)", e);
+    return QCMET_OK;
+}
+
+int launch(qcmet_batch &b, int32_t T, int32_t threads, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_err("cudaMemsetAsync(batch counter)", e);
+    qcmet::BatchArgs a;
+    a.frames = b.d_frames;
+    a.order = b.d_order;
+    a.counter = b.d_counter;
+    a.K = b.K;
+    a.T = T;
+    std::string err;
+    int st = qcmet::launch_decode_batch(a, b.fmt, threads, b.max_image_words, s, err);
+    if (st) return qcmet::set_error(st, err);
+    return QCMET_OK;
+}
+
+void release(qcmet_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->d_scratch) cudaFree(b->d_scratch);
+    for (qcmet_code *a : b->alt)
+        if (a) qcmet_code_destroy(a);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
+                       int32_t msg_format, int32_t autotune, void *stream, qcmet_batch **out) {
+    if (!out) return qcmet::set_error(QCMET_ERR_INVALID_ARG, "out must not be NULL");
+    *out = nullptr;
+    if (!frames || K < 1 || iterations < 0)
+        return qcmet::set_error(QCMET_ERR_INVALID_ARG, "need frames, K >= 1 and iterations >= 0");
+    if (msg_format != QCMET_MSG_FP32 && msg_format != QCMET_MSG_FP16 && msg_format != QCMET_MSG_BF16)
+        return qcmet::set_error(QCMET_ERR_INVALID_ARG, "unknown msg_format");
+    qcmet_batch *b = new (std::nothrow) qcmet_batch;
+    if (!b) return qcmet::set_error(QCMET_ERR_OOM, "host allocation failed");
+    b->frames.assign(frames, frames + K);
+    b->K = K;
+    b->T = iterations;
+    b->fmt = msg_format;
+    std::map<const qcmet_code *, int32_t> ids;
+    size_t bytes = 0;
+    for (int32_t k = 0; k < K; ++k) {
+        const qcmet_frame &f = frames[k];
+        auto bad = [](const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; };
+        if (!f.code || !f.llr_ch || !f.syndrome || !f.hard || !f.ok) {
+            release(b);
+            return qcmet::set_error(QCMET_ERR_INVALID_ARG, "frame " + std::to_string(k) +
+                                                              ": code, llr_ch, syndrome, hard and ok must not be NULL");
+        }
+        if (bad(f.llr_ch) || bad(f.syndrome) || bad(f.hard) || bad(f.ok) ||
+            (f.llr_post && bad(f.llr_post))) {
+            release(b);
+            return qcmet::set_error(QCMET_ERR_ALIGNMENT, "frame " + std::to_string(k) +
+                                                            ": device pointers must be 16-byte aligned");
+        }
+        auto it = ids.find(f.code);
+        if (it == ids.end()) {
+            it = ids.emplace(f.code, (int32_t)b->codes.size()).first;
+            b->codes.push_back(f.code);
+        }
+        b->frame_code.push_back(it->second);
+        const qcmet::Code &c = f.code->c;
+        bytes += r256((size_t)c.msg_slots * qcmet::slot_stride(c.Z) * msg_size(msg_format));
+        if (!f.llr_post) bytes += r256((size_t)c.nb * c.Z * sizeof(float));
+    }
+    // the other exact schedule of each code (base-row order <-> merged), for the autotuner
+    for (const qcmet_code *h : b->codes) {
+        const qcmet::Code &c = h->c;
+        qcmet_code *alt = nullptr;
+        if (autotune && c.merge_mode != QCMET_MERGE_GREEDY) {
+            const int32_t other = c.merge_mode == QCMET_MERGE_EXACT ? QCMET_MERGE_NONE : QCMET_MERGE_EXACT;
+            int st = qcmet_code_create_ex(c.base.data(), c.shifts.data(), c.mb, c.nb, c.Z, other, &alt);
+            if (st) {
+                release(b);
+                return st;
+            }
+        }
+        b->alt.push_back(alt);
+    }
+    const size_t desc = r256((size_t)K * sizeof(qcmet::BatchFrame));
+    const size_t ord = r256((size_t)K * sizeof(int32_t));
+    cudaError_t e = cudaMalloc(&b->d_scratch, bytes + desc + ord + 256);
+    if (e != cudaSuccess) {
+        release(b);
+        return cuda_err("cudaMalloc(batch scratch)", e);
+    }
+    char *base = static_cast<char *>(b->d_scratch);
+    b->d_frames = reinterpret_cast<qcmet::BatchFrame *>(base + bytes);
+    b->d_order = reinterpret_cast<int32_t *>(base + bytes + desc);
+    b->d_counter = reinterpret_cast<int32_t *>(base + bytes + desc + ord);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // candidates: block size x schedule variant x frame order (all give the same results)
+    struct Cand { int32_t threads; bool alt; bool largest; };
+    std::vector<Cand> cands;
+    if (autotune) {
+        for (int32_t th : {512, 1024})
+            for (bool alt : {false, true})
+                for (bool lf : {true, false})
+                    if (!alt || std::any_of(b->alt.begin(), b->alt.end(), [](qcmet_code *a) { return a != nullptr; }))
+                        cands.push_back({th, alt, lf});
+    } else {
+        cands.push_back({1024, false, true});
+    }
+    Cand best = cands[0];
+    float best_ms = -1.0f;
+    if (cands.size() > 1) {
+        const int32_t Tt = std::min<int32_t>(iterations, 4);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        for (const Cand &c : cands) {
+            int st = write_descriptors(*b, c.alt, c.largest, s);
+            if (!st) st = launch(*b, Tt, c.threads, s);   // warm-up
+            if (!st) {
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 2 && !st; ++r) st = launch(*b, Tt, c.threads, s);
+                cudaEventRecord(e1, s);
+            }
+            if (st) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                release(b);
+                return st;
+            }
+            cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best_ms < 0.0f || ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    int st = write_descriptors(*b, best.alt, best.largest, s);
+    if (st) {
+        release(b);
+        return st;
+    }
+    b->cfg.threads_per_block = best.threads;
+    b->cfg.alternate_schedule = best.alt ? 1 : 0;
+    b->cfg.largest_first = best.largest ? 1 : 0;
+    b->cfg.trial_ms = best_ms;
+    b->cfg.candidates = (int32_t)cands.size();
+
+    // capture counter reset + launch into a graph on a private stream
+    cudaStream_t cap;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        release(b);
+        return cuda_err("cudaStreamCreateWithFlags", e);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = launch(*b, iterations, best.threads, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+        if (!st && e2 != cudaSuccess) st = cuda_err("cudaStreamEndCapture", e2);
+    } else {
+        st = cuda_err("cudaStreamBeginCapture", e);
+    }
+    if (!st) {
+        e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (e != cudaSuccess) st = cuda_err("cudaGraphInstantiate", e);
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    if (st) {
+        release(b);
+        return st;
+    }
+    *out = b;
+    return QCMET_OK;
+}
+
+int qcmet_batch_run(qcmet_batch *batch, void *stream) {
+    if (!batch || !batch->exec) return qcmet::set_error(QCMET_ERR_INVALID_ARG, "batch must not be NULL");
+    cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_err("cudaGraphLaunch", e);
+    return QCMET_OK;
+}
+
+int qcmet_batch_get_config(const qcmet_batch *batch, qcmet_batch_config *out) {
+    if (!batch || !out) return qcmet::set_error(QCMET_ERR_INVALID_ARG, "batch and out must not be NULL");
+    *out = batch->cfg;
+    return QCMET_OK;
+}
+
+void qcmet_batch_destroy(qcmet_batch *batch) { release(batch); }
+
+}  // extern "C"

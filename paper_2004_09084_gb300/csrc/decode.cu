@@ -448,6 +448,68 @@ __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, 
     return __syncthreads_or(fail);
 }
 
+// Decode frame f of `a` (steps 1-4) with the schedule `s` already in shared
+// memory.  Called by every thread of the block.
+template <typename M>
+__device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArgs &a, int f) {
+    const int Z = s.Z;
+    const size_t n = (size_t)a.n;
+    const size_t stride = (size_t)a.slot_stride;
+    const int T = a.T;
+    Frame<M> fr;
+    fr.ch = a.ch + (size_t)f * n;
+    fr.syn = a.syn + (size_t)f * (size_t)a.m;
+    fr.post = a.post + (size_t)f * n;
+    fr.msg = static_cast<M *>(a.msgs) + (size_t)f * (size_t)a.msg_slots * stride;
+
+    // Step 1: L_qn = channel LLR for every variable that carries state.
+    for (int c = 0; c < s.nb; ++c) {
+        if (s.col_kind[c] != kColCore) continue;
+        const float *src = fr.ch + (size_t)c * Z;
+        float *dst = fr.post + (size_t)c * Z;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
+    }
+    if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
+    __syncthreads();
+
+    // Steps 2-3 over T iterations x layers.  With early termination
+    // (Discussion, Table tabearly) every check_every-th iteration ends with
+    // the hard decision and syndrome test, and a frame that passes stops.
+    // Those iterations, like the last one, also write the posteriors of the
+    // degree-1 columns, which the test needs.
+    int t_stop = T;
+    bool tested = false;
+    for (int t = 0; t < T; ++t) {
+        const bool first = t == 0;
+        const bool final_iter = t == T - 1;
+        const bool check = final_iter || (a.check_every > 0 && (t + 1) % a.check_every == 0);
+        for (int layer = 0; layer < s.n_layers; ++layer) {
+            for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
+                if (threadIdx.x < 32) {
+                    if (j + 1 < s.n_rows) prefetch_row<M>(s, a, f, j + 1, t);
+                    else if (!final_iter) prefetch_row<M>(s, a, f, 0, t + 1);
+                }
+                const int4 row = s.rows[j];
+                dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
+            }
+            __syncthreads();
+        }
+        if (a.check_every > 0 && check && !final_iter &&
+            finalize_frame<M>(s, a, fr, f, false) == 0) {
+            t_stop = t + 1;
+            tested = true;
+            break;
+        }
+    }
+
+    const int fail = tested ? 0 : finalize_frame<M>(s, a, fr, f, T == 0);
+    if (threadIdx.x == 0) {
+        a.ok[f] = fail ? 0 : 1;
+        if (a.iters_used) a.iters_used[f] = t_stop;
+    }
+    __syncthreads();
+}
+
 template <typename M>
 __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a) {
     extern __shared__ int4 smem_i4[];
@@ -458,64 +520,53 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
     }
     __syncthreads();
     const Sched s = make_sched(sw);
-    const int Z = s.Z;
-    const size_t n = (size_t)a.n;
-    const size_t stride = (size_t)a.slot_stride;
-    const int T = a.T;
+    for (int f = blockIdx.x; f < a.K; f += gridDim.x) decode_one_frame<M>(s, a, f);
+}
 
-    for (int f = blockIdx.x; f < a.K; f += gridDim.x) {
-        Frame<M> fr;
-        fr.ch = a.ch + (size_t)f * n;
-        fr.syn = a.syn + (size_t)f * (size_t)a.m;
-        fr.post = a.post + (size_t)f * n;
-        fr.msg = static_cast<M *>(a.msgs) + (size_t)f * (size_t)a.msg_slots * stride;
-
-        // Step 1: L_qn = channel LLR for every variable that carries state.
-        for (int c = 0; c < s.nb; ++c) {
-            if (s.col_kind[c] != kColCore) continue;
-            const float *src = fr.ch + (size_t)c * Z;
-            float *dst = fr.post + (size_t)c * Z;
-            for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
-        }
-        if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
+// Mixed batch: frames of several codes in one launch.  Persistent CTAs take
+// frames in the order given (largest first by default) from an atomic
+// counter -- a work queue, nothing waits on another CTA -- load the frame's
+// layer table into shared memory when the code changes, and decode it.
+template <typename M>
+__global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const BatchArgs b) {
+    extern __shared__ int4 smem_i4[];
+    int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
+    __shared__ int s_next;
+    int cur_code = -1;
+    for (;;) {
+        if (threadIdx.x == 0) s_next = atomicAdd(b.counter, 1);
         __syncthreads();
-
-        // Steps 2-3 over T iterations x layers.  With early termination
-        // (Discussion, Table tabearly) every check_every-th iteration ends with
-        // the hard decision and syndrome test, and a frame that passes stops.
-        // Those iterations, like the last one, also write the posteriors of the
-        // degree-1 columns, which the test needs.
-        int t_stop = T;
-        bool tested = false;
-        for (int t = 0; t < T; ++t) {
-            const bool first = t == 0;
-            const bool final_iter = t == T - 1;
-            const bool check = final_iter || (a.check_every > 0 && (t + 1) % a.check_every == 0);
-            for (int layer = 0; layer < s.n_layers; ++layer) {
-                for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
-                    if (threadIdx.x < 32) {
-                        if (j + 1 < s.n_rows) prefetch_row<M>(s, a, f, j + 1, t);
-                        else if (!final_iter) prefetch_row<M>(s, a, f, 0, t + 1);
-                    }
-                    const int4 row = s.rows[j];
-                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
-                }
-                __syncthreads();
-            }
-            if (a.check_every > 0 && check && !final_iter &&
-                finalize_frame<M>(s, a, fr, f, false) == 0) {
-                t_stop = t + 1;
-                tested = true;
-                break;
-            }
-        }
-
-        const int fail = tested ? 0 : finalize_frame<M>(s, a, fr, f, T == 0);
-        if (threadIdx.x == 0) {
-            a.ok[f] = fail ? 0 : 1;
-            if (a.iters_used) a.iters_used[f] = t_stop;
-        }
+        const int k = s_next;
         __syncthreads();
+        if (k >= b.K) break;
+        const BatchFrame fd = b.frames[b.order[k]];
+        if (fd.code_id != cur_code) {
+            const int4 *src = reinterpret_cast<const int4 *>(fd.image);
+            for (int w = threadIdx.x; w < fd.image_words / 4; w += blockDim.x) smem_i4[w] = src[w];
+            __syncthreads();
+            cur_code = fd.code_id;
+        }
+        const Sched s = make_sched(sw);
+        DecodeArgs a;
+        a.ch = fd.ch;
+        a.syn = fd.syn;
+        a.post = fd.post;
+        a.msgs = fd.msgs;
+        a.hard = fd.hard;
+        a.ok = fd.ok;
+        a.image = fd.image;
+        a.image_words = fd.image_words;
+        a.K = 1;
+        a.T = b.T;
+        a.Z = fd.Z;
+        a.n = fd.n;
+        a.m = fd.m;
+        a.nb = fd.nb;
+        a.msg_slots = fd.msg_slots;
+        a.slot_stride = fd.slot_stride;
+        a.check_every = 0;
+        a.iters_used = nullptr;
+        decode_one_frame<M>(s, a, 0);
     }
 }
 
@@ -555,7 +606,52 @@ int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &er
     return QCMET_OK;
 }
 
+template <typename M>
+int launch_batch_typed(const BatchArgs &b, int threads, int grid, size_t smem, void *stream,
+                       std::string &err) {
+    auto kern = decode_batch_kernel<M>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) {
+            err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return QCMET_ERR_UNSUPPORTED;
+        }
+    }
+    kern<<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("batch decode launch: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    return QCMET_OK;
+}
+
 }  // namespace
+
+int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
+                        int32_t max_image_words, void *stream, std::string &err) {
+    if (threads == 0) threads = kDefaultThreads;
+    if (threads < 32 || threads > kDefaultThreads || threads % 32) {
+        err = "threads_per_block must be a multiple of 32 in [32, 1024]";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    const int sms = sm_count_cached();
+    if (sms <= 0) {
+        err = "no CUDA device";
+        return QCMET_ERR_CUDA;
+    }
+    const int grid = b.K < sms ? b.K : sms;
+    if (grid <= 0) return QCMET_OK;
+    const size_t smem = (size_t)max_image_words * sizeof(int32_t);
+    switch (msg_format) {
+        case QCMET_MSG_FP32: return launch_batch_typed<float>(b, threads, grid, smem, stream, err);
+        case QCMET_MSG_FP16: return launch_batch_typed<__half>(b, threads, grid, smem, stream, err);
+        case QCMET_MSG_BF16:
+            return launch_batch_typed<__nv_bfloat16>(b, threads, grid, smem, stream, err);
+        default: err = "unknown message format"; return QCMET_ERR_INVALID_ARG;
+    }
+}
 
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
                   std::string &err) {

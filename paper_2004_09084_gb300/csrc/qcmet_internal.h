@@ -115,6 +115,11 @@ struct Code {
     LearnedArgs learned_last{};
 };
 
+// Shared by the C ABI files (api.cpp, batch.cpp): upload a code's layer table
+// once per device, and record a failing call's message for qcmet_last_error.
+int ensure_device_image(Code &c);
+int set_error(int status, const std::string &msg);
+
 // Host builder (layout.cpp).  Returns a QCMET status; fills `err` on failure.
 int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb, int32_t Z,
                int32_t merge_mode, Code &code, std::string &err);
@@ -143,6 +148,33 @@ struct DecodeArgs {
 int launch_learned_forward(const LearnedArgs &a, bool train, void *stream, std::string &err);
 int launch_learned_backward(const LearnedArgs &a, void *stream, std::string &err);
 
+// One frame of a mixed batch (device array; decode.cu's batch kernel).
+struct BatchFrame {
+    const int32_t *image;    // the frame's code: schedule image (device)
+    const float *ch;         // [n]
+    const uint8_t *syn;      // [m]
+    float *post;             // [n]
+    uint8_t *hard;           // [n]
+    uint8_t *ok;             // [1]
+    void *msgs;              // [msg_slots][slot_stride] messages
+    int64_t slot_stride;
+    int32_t image_words;
+    int32_t code_id;         // frames with equal code_id share the image
+    int32_t Z, n, m, nb;
+    int32_t msg_slots;
+    int32_t pad;
+};
+
+struct BatchArgs {
+    const BatchFrame *frames;  // [K]
+    const int32_t *order;      // [K] frame indices in the order CTAs take them
+    int32_t *counter;          // work counter (zero before the launch)
+    int32_t K, T;
+};
+
+int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
+                        int32_t max_image_words, void *stream, std::string &err);
+
 // Launch the fused decode kernel for one message format (decode.cu).
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
                   std::string &err);
@@ -154,3 +186,8 @@ int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_
 size_t noalloc_capacity_bytes();
 
 }  // namespace qcmet
+
+// The opaque handle of the C ABI.
+struct qcmet_code {
+    qcmet::Code c;
+};
