@@ -242,7 +242,7 @@ def run_ours(args):
 
     def step():
         q.decode(qc, llr, syn, ITERS, hard=hard, llr_post=post, ok=ok, msg=args.msg,
-                 stream=stream)
+                 stream=stream, l2_persist=args.l2_persist == "on")
 
     progress("inputs resident; warm-up")
     for _ in range(args.warmup):
@@ -282,13 +282,13 @@ def run_ours(args):
     pin_ok = torch.empty((K_FRAMES,), dtype=torch.uint8).pin_memory()
     host_out = (pin_hard.numpy(), None, pin_ok.numpy())
     q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
-                  stream=stream, out=host_out)
+                  stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
-                      stream=stream, out=host_out)
+                      stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     h2d = K_FRAMES * n * 4 + K_FRAMES * code.m
     d2h = K_FRAMES * n + K_FRAMES
@@ -322,6 +322,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args.msg), "K": K_FRAMES, "Z": Z, "n": n,
                        "iterations": ITERS, "snr": SNR, "msg": args.msg,
+                       "l2_persist": args.l2_persist,
                        "parallelism": f"dp{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (message state "
                              f"{K_FRAMES * info['msg_slots'] * Z * mbytes / 1e9:.2f} GB per GPU)"},
@@ -357,11 +358,13 @@ def run_profile(args):
     syn = torch.from_numpy(fr.syn).to(dev)
     progress("profile case: inputs resident")
     for k in range(args.launches):
-        hard, post, ok = q.decode(qc, llr, syn, args.iters, msg=args.msg)
+        hard, post, ok = q.decode(qc, llr, syn, args.iters, msg=args.msg,
+                                  l2_persist=args.l2_persist == "on")
         torch.cuda.synchronize(dev)
         progress(f"profile case: launch {k} done")
     print(json.dumps({"profile_case": {"frames": args.frames, "iters": args.iters,
                                        "launches": args.launches, "msg": args.msg,
+                                       "l2_persist": args.l2_persist,
                                        "ok_rate": float(ok.float().mean().item())}}))
     return 0
 
@@ -525,6 +528,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--msg", choices=["fp32", "fp16", "bf16"], default="fp32")
+    ap.add_argument("--l2-persist", choices=["on", "off"], default="on",
+                    help="persisting L2 window over the core posteriors")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only run --launches decodes of --frames x --iters (for ncu captures)")

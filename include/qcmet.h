@@ -113,10 +113,20 @@ int qcmet_code_get_info(const qcmet_code *code, qcmet_code_info *info);
  */
 int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *layer_first);
 
+/*
+ * l2_persist = 1 asks the decode kernel to keep the posteriors of the core
+ * columns (K * core_columns * Z floats, the state every layer re-reads) in L2:
+ * the launch carries a persisting access-policy window over them.  The first
+ * such call raises the calling context's persisting-L2 limit
+ * (cudaLimitPersistingL2CacheSize) to the window size when it is lower; that
+ * limit belongs to the CUDA context and ends with it.  On a device without
+ * persisting L2 the option is ignored.  It changes no result, only speed.
+ */
 typedef struct {
     int32_t msg_format;        /* QCMET_MSG_*; 0 = FP32                               */
     int32_t threads_per_block; /* 0 = library default; else a multiple of 32, <= 1024 */
-    int32_t reserved[6];       /* set to 0                                          */
+    int32_t l2_persist;        /* 0 = off, 1 = persisting L2 window over the state  */
+    int32_t reserved[5];       /* set to 0                                          */
 } qcmet_decode_options;
 
 /*
@@ -188,15 +198,17 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
  *
  * Its scratch is one fixed array of 32 MiB that the library defines in device
  * memory; every GPU that loads the library holds it until the process exits.
- * 64 KiB of it hold a copy of the code's layer table, the rest the messages:
- * the call needs K * msg_slots * roundup(Z, 16) * 4 bytes of the remaining
- * 32 MiB - 64 KiB and returns QCMET_ERR_INVALID_ARG, with a message that
- * states both sizes, when that does not fit (e.g. at Z = 12500 and 230 slots
- * it takes at most 2 frames per call; at Z = 64, over 500).
+ * 64 KiB of it hold a copy of the code's layer table, the rest the messages
+ * and the posteriors of the core columns (degree > 1): the call needs
+ * roundup(K * msg_slots * roundup(Z, 16) * 4, 256) + K * core_columns * Z * 4
+ * bytes of the remaining 32 MiB - 64 KiB and returns QCMET_ERR_INVALID_ARG,
+ * with a message that states both sizes, when that does not fit (e.g. at
+ * Z = 12500, 230 slots and 10 core columns it takes at most 2 frames per
+ * call; at Z = 64, over 400).
  *
  * Arguments, layouts and results are those of qcmet_decode, except that
- * llr_post must not be NULL (it holds the posteriors while decoding) and no
- * options are taken (FP32 messages, default block size).  The results equal
+ * llr_post must not be NULL (the degree-1 posteriors are written there while
+ * decoding) and no options are taken (FP32 messages, default block size).  The results equal
  * qcmet_decode's bit for bit.
  *
  * All calls share the one array and it keeps what the last call left; this

@@ -78,7 +78,7 @@ class BatchConfig(ctypes.Structure):
 
 class DecodeOptions(ctypes.Structure):
     _fields_ = [("msg_format", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 def _load():
@@ -193,23 +193,26 @@ class Code:
             pass
 
 
-def _options(msg: str, threads: int) -> DecodeOptions:
+def _options(msg: str, threads: int, l2_persist: bool = False) -> DecodeOptions:
     if msg not in MSG:
         raise ValueError(f"msg must be one of {sorted(MSG)}")
     o = DecodeOptions()
     o.msg_format = MSG[msg]
     o.threads_per_block = int(threads)
+    o.l2_persist = 1 if l2_persist else 0
     return o
 
 
 def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=None,
-           msg: str = "fp32", threads: int = 0, stream=None, want_post: bool = True):
+           msg: str = "fp32", threads: int = 0, stream=None, want_post: bool = True,
+           l2_persist: bool = False):
     """Decode K frames on the GPU (``qcmet_decode_ex``).
 
     ``llr``: float32 CUDA tensor [K, n]; ``syn``: uint8 CUDA tensor [K, m].
     Outputs are allocated when not given.  Returns ``(hard, llr_post, ok)``
     (``llr_post`` is None when ``want_post`` is false and none was passed).
     The call is asynchronous on ``stream`` (default: torch's current stream).
+    ``l2_persist`` keeps the core posteriors in a persisting L2 window.
     """
     import torch
 
@@ -234,7 +237,7 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    opts = _options(msg, threads)
+    opts = _options(msg, threads, l2_persist)
     _check(lib.qcmet_decode_ex(code.handle, llr.data_ptr(), syn.data_ptr(), K, int(iterations),
                                hard.data_ptr(), llr_post.data_ptr() if llr_post is not None else None,
                                ok.data_ptr(), ctypes.byref(opts), sptr))
@@ -275,7 +278,7 @@ def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: in
 
 def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
                 want_post: bool = True, msg: str = "fp32", threads: int = 0, stream=None,
-                out=None):
+                out=None, l2_persist: bool = False):
     """Decode frames held in host memory (``qcmet_decode_host``); synchronous.
 
     ``out`` may supply preallocated (hard, llr_post, ok) host arrays, e.g. pinned.
@@ -291,7 +294,7 @@ def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
     for a, dt in ((llr, np.float32), (syn, np.uint8), (hard, np.uint8), (ok, np.uint8)):
         if a.dtype != dt or not a.flags.c_contiguous:
             raise ValueError("host arrays must be C-contiguous with the documented dtypes")
-    opts = _options(msg, threads)
+    opts = _options(msg, threads, l2_persist)
     sptr = 0
     if stream is not None:
         sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

@@ -3,6 +3,7 @@
 // the fused kernel in decode.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -73,9 +74,11 @@ int grow(void **buf, size_t *have, size_t need, const char *what) {
     return QCMET_OK;
 }
 
-int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads) {
+int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
+                  bool *l2_persist = nullptr) {
     *fmt = QCMET_MSG_FP32;
     *threads = 0;
+    if (l2_persist) *l2_persist = false;
     if (!o) return QCMET_OK;
     if (o->msg_format != QCMET_MSG_FP32 && o->msg_format != QCMET_MSG_FP16 &&
         o->msg_format != QCMET_MSG_BF16)
@@ -83,10 +86,46 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads)
     if (o->threads_per_block != 0 &&
         (o->threads_per_block < 32 || o->threads_per_block > 1024 || o->threads_per_block % 32))
         return fail(QCMET_ERR_INVALID_ARG, "threads_per_block must be 0 or a multiple of 32 in [32, 1024]");
+    if (o->l2_persist != 0 && o->l2_persist != 1)
+        return fail(QCMET_ERR_INVALID_ARG, "l2_persist must be 0 or 1");
     for (int32_t r : o->reserved)
         if (r != 0) return fail(QCMET_ERR_INVALID_ARG, "reserved option fields must be 0");
     *fmt = o->msg_format;
     *threads = o->threads_per_block;
+    if (l2_persist) *l2_persist = o->l2_persist == 1;
+    return QCMET_OK;
+}
+
+// Size an L2 persisting window over `bytes` of decoder state on the current
+// device: the window is capped by the device's largest window, the persisting
+// part of L2 is raised (for this context) to cover it where the device allows,
+// and the hit ratio is the fraction of the window that fits in that part.
+// A device without persisting L2 gets no window (window = 0).
+int l2_window(size_t bytes, size_t *window, float *hit) {
+    *window = 0;
+    *hit = 0.0f;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    int max_persist = 0, max_window = 0;
+    e = cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute(persisting L2)", e);
+    e = cudaDeviceGetAttribute(&max_window, cudaDevAttrMaxAccessPolicyWindowSize, dev);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetAttribute(access policy window)", e);
+    if (max_persist <= 0 || max_window <= 0 || bytes == 0) return QCMET_OK;
+    const size_t w = std::min(bytes, (size_t)max_window);
+    size_t limit = 0;
+    e = cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceGetLimit(persisting L2)", e);
+    const size_t want = std::min(w, (size_t)max_persist);
+    if (limit < want) {
+        e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
+        if (e != cudaSuccess) return cuda_fail("cudaDeviceSetLimit(persisting L2)", e);
+        e = cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
+        if (e != cudaSuccess) return cuda_fail("cudaDeviceGetLimit(persisting L2)", e);
+    }
+    *window = w;
+    *hit = limit >= w ? 1.0f : (float)((double)limit / (double)w);
     return QCMET_OK;
 }
 
@@ -95,7 +134,8 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
                   const qcmet_decode_options *opts, void *stream, int32_t check_every = 0,
                   int32_t *iters_used = nullptr) {
     int32_t fmt, threads;
-    int st = check_options(opts, &fmt, &threads);
+    bool l2p = false;
+    int st = check_options(opts, &fmt, &threads, &l2p);
     if (st) return st;
     if (K < 0) return fail(QCMET_ERR_INVALID_ARG, "K must be >= 0");
     if (T < 0) return fail(QCMET_ERR_INVALID_ARG, "iterations must be >= 0");
@@ -121,11 +161,25 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
         if (st) return st;
         post = c.d_post;
     }
+    const size_t need_core = (size_t)K * (size_t)c.core_cols * (size_t)c.Z * sizeof(float);
+    {
+        void *p = c.d_core;
+        st = grow(&p, &c.core_bytes, need_core ? need_core : 16, "cudaMalloc(core posteriors)");
+        c.d_core = static_cast<float *>(p);
+        if (st) return st;
+    }
+    size_t window = 0;
+    float hit = 0.0f;
+    if (l2p) {
+        st = l2_window(need_core, &window, &hit);
+        if (st) return st;
+    }
 
     qcmet::DecodeArgs a;
     a.ch = llr_ch;
     a.syn = syndrome;
     a.post = post;
+    a.post_core = c.d_core;
     a.msgs = c.d_msgs;
     a.hard = hard;
     a.ok = ok;
@@ -138,11 +192,12 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     a.m = c.mb * c.Z;
     a.nb = c.nb;
     a.msg_slots = c.msg_slots;
+    a.core_cols = c.core_cols;
     a.slot_stride = (int64_t)stride;
     a.check_every = check_every;
     a.iters_used = iters_used;
     std::string err;
-    st = qcmet::launch_decode(a, fmt, threads, stream, err);
+    st = qcmet::launch_decode(a, fmt, threads, stream, err, window, hit);
     if (st) return fail(st, err);
     return QCMET_OK;
 }
@@ -191,6 +246,7 @@ void qcmet_code_destroy(qcmet_code *code) {
     if (c.d_image) cudaFree(c.d_image);
     if (c.d_msgs) cudaFree(c.d_msgs);
     if (c.d_post) cudaFree(c.d_post);
+    if (c.d_core) cudaFree(c.d_core);
     if (c.d_io) cudaFree(c.d_io);
     if (c.d_learned) cudaFree(c.d_learned);
     delete code;
@@ -321,7 +377,8 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
     a.ch = llr_ch;
     a.syn = syndrome;
     a.post = llr_post;
-    a.msgs = nullptr;   // set by the launcher: inside the static scratch
+    a.post_core = nullptr;  // set by the launcher: inside the static scratch
+    a.msgs = nullptr;       // set by the launcher: inside the static scratch
     a.hard = hard;
     a.ok = ok;
     a.image = nullptr;  // set by the launcher: a copy inside the static scratch
@@ -333,6 +390,7 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
     a.m = c.mb * c.Z;
     a.nb = c.nb;
     a.msg_slots = c.msg_slots;
+    a.core_cols = c.core_cols;
     a.slot_stride = (int64_t)qcmet::slot_stride(c.Z);
     a.check_every = 0;
     a.iters_used = nullptr;

@@ -63,9 +63,12 @@ int write_descriptors(qcmet_batch &b, bool alt, bool largest_first, cudaStream_t
         d.m = c.mb * c.Z;
         d.nb = c.nb;
         d.msg_slots = c.msg_slots;
+        d.core_cols = c.core_cols;
         d.slot_stride = (int64_t)qcmet::slot_stride(c.Z);
         d.msgs = p + off;
         off += r256((size_t)c.msg_slots * (size_t)d.slot_stride * msg_size(b.fmt));
+        d.post_core = reinterpret_cast<float *>(p + off);
+        off += r256((size_t)c.core_cols * (size_t)c.Z * sizeof(float));
         if (f.llr_post) {
             d.post = f.llr_post;
         } else {
@@ -158,6 +161,7 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
         b->frame_code.push_back(it->second);
         const qcmet::Code &c = f.code->c;
         bytes += r256((size_t)c.msg_slots * qcmet::slot_stride(c.Z) * msg_size(msg_format));
+        bytes += r256((size_t)c.core_cols * (size_t)c.Z * sizeof(float));
         if (!f.llr_post) bytes += r256((size_t)c.nb * c.Z * sizeof(float));
     }
     // the other exact schedule of each code (base-row order <-> merged), for the autotuner

@@ -12,10 +12,13 @@
 //  * Frames are independent, so one CTA owns one frame for the whole decode
 //    and a layer boundary costs one block barrier.  The whole decode -- init,
 //    T x layers, hard decision, syndrome test -- is a single launch.
-//  * Frame-major state: posteriors L_qn [K][n] live in the caller's llr_post
-//    buffer (FP32), messages [K][slot][Z] in FP32 / FP16 / BF16.  Within a
-//    circulant, consecutive checks touch consecutive variables, so a warp's
-//    gathers are contiguous runs of 128 B (one wrap at most).
+//  * Frame-major state: the posteriors L_qn of the core columns (degree > 1)
+//    live in a compact array [K][core_cols][Z] (FP32), messages [K][slot][Z]
+//    in FP32 / FP16 / BF16.  The compact array is the state every row
+//    re-reads, so it is one contiguous range that an L2 persisting window can
+//    cover; the caller's llr_post [K][n] receives the posteriors at the end.
+//    Within a circulant, consecutive checks touch consecutive variables, so a
+//    warp's gathers are contiguous runs of 128 B (one wrap at most).
 //  * Degree-1 variables (a base column with a single circulant) keep no state:
 //    for them L_qn - L_rmn(old) equals the channel LLR exactly, so q is read
 //    from the channel array and L_qn is written once, in the last iteration.
@@ -51,7 +54,10 @@ constexpr float kClipMax = 30.0f;
 constexpr float kClipMin = 1.8715246e-13f;
 constexpr float kLn2 = 0.693147180559945309f;
 constexpr float kLog2e = 1.442695040888963407f;
-constexpr int kDefaultThreads = 1024;
+#ifndef QCMET_THREADS
+#define QCMET_THREADS 1024
+#endif
+constexpr int kDefaultThreads = QCMET_THREADS;
 
 // ---- message storage formats ---------------------------------------------
 
@@ -117,6 +123,7 @@ struct Sched {
     const int4 *entries;  // DevEntry
     const int32_t *col_kind;
     const int32_t *zero_rows;
+    const int32_t *col_core;  // [nb]: index among the core columns, or -1
 };
 
 __device__ __forceinline__ Sched make_sched(const int32_t *w) {
@@ -133,6 +140,7 @@ __device__ __forceinline__ Sched make_sched(const int32_t *w) {
     s.entries = reinterpret_cast<const int4 *>(w + w[kHdrOffEntries]);
     s.col_kind = w + w[kHdrOffColKind];
     s.zero_rows = w + w[kHdrOffZeroRows];
+    s.col_core = w + w[kHdrOffColCore];
     return s;
 }
 
@@ -141,7 +149,8 @@ template <typename M>
 struct Frame {
     const float *ch;     // [n]
     const uint8_t *syn;  // [m]
-    float *post;         // [n]
+    float *post;         // [n] output posteriors (degree-1 columns written in place)
+    float *post_core;    // [core_cols][Z] posteriors of the core columns
     M *msg;              // [slots][stride]
 };
 
@@ -204,7 +213,7 @@ __device__ __forceinline__ float gather_q(const int4 &en, int i, const Frame<M> 
     j = j >= Z ? j - Z : j;
     const int v = en.x + j;
     if (en.z < 0) return __ldcs(fr.ch + v);  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
-    const float lv = fr.post[v];
+    const float lv = fr.post_core[v];
     const float ro = first ? 0.0f : Msg<M>::load(fr.msg + (size_t)en.z * stride + i);
     return lv - ro;
 }
@@ -225,8 +234,10 @@ __device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float 
     if (en.z >= 0) {
         rn = Msg<M>::quantize(rn);
         Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
+        fr.post_core[v] = q + rn;
+    } else {
+        fr.post[v] = q + rn;
     }
-    fr.post[v] = q + rn;
 }
 
 __device__ __forceinline__ float u_of(float q) {
@@ -237,7 +248,10 @@ __device__ __forceinline__ float u_of(float q) {
 // inputs of U checks (i, i + NT, ..., i + (U-1) NT) in straight-line code --
 // the source array of an edge is selected, not branched on, and checks past Z
 // load from a clamped (valid) index -- so that all U * (2D + 1) loads are in
-// flight together; then it computes and writes the U checks.
+// flight together; then it computes and writes the U checks.  (Issuing the
+// next batch's loads before computing the current one measured slower at
+// every block size: at 1024 threads it spills, and fewer threads leave too
+// few warps to hide the arithmetic's own latency.)
 //   first: iteration 0 (old messages are zero and are not read)
 //   last : final iteration (degree-1 variables get their posterior)
 #ifndef QCMET_BATCH_LOW
@@ -265,7 +279,7 @@ __device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_
                 int j = i + en.y;
                 j = j >= Z ? j - Z : j;
                 // degree-1 variable: L_qn - L_rmn(old) is the channel LLR exactly
-                const float *src = en.z < 0 ? fr.ch : fr.post;
+                const float *src = en.z < 0 ? fr.ch : fr.post_core;
                 lv[k][e] = src[en.x + j];
                 const bool has_old = !first && en.z >= 0;
                 ro[k][e] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + i) : 0.0f;
@@ -379,9 +393,9 @@ __device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a
     const size_t Z = (size_t)s.Z;
     const size_t n = (size_t)a.n;
     const size_t fl_bytes = (size_t)a.K * n * sizeof(float);
+    const size_t nc = (size_t)a.core_cols * Z;
     if (lane < row.y) {
         const int4 en = s.entries[row.x + lane];
-        const size_t col_off = ((size_t)f * n + (size_t)en.x) * sizeof(float);
         if (en.z >= 0) {
             if (t > 0) {
                 const M *slot = static_cast<const M *>(a.msgs) +
@@ -389,18 +403,21 @@ __device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a
                 // the slot stride is a multiple of 16 elements: the widened range stays inside it
                 prefetch_l2(slot, ((Z * sizeof(M)) + 15) & ~size_t(15), 0, Z * sizeof(M));
             }
-            prefetch_l2(a.post, fl_bytes, col_off, Z * sizeof(float));
+            prefetch_l2(a.post_core, (size_t)a.K * nc * sizeof(float),
+                        ((size_t)f * nc + (size_t)en.x) * sizeof(float), Z * sizeof(float));
         } else {
-            prefetch_l2(a.ch, fl_bytes, col_off, Z * sizeof(float));
+            prefetch_l2(a.ch, fl_bytes, ((size_t)f * n + (size_t)en.x) * sizeof(float),
+                        Z * sizeof(float));
         }
     } else if (lane == 31) {
         prefetch_l2(a.syn, (size_t)a.K * (size_t)a.m, (size_t)f * a.m + (size_t)row.z, Z);
     }
 }
 
-// Step 4 for frame f: posteriors of the columns that carry no state, hard
-// decisions c_n = [L_qn < 0], and the syndrome test.  Returns, identically in
-// every thread of the block, nonzero when H c != s.
+// Step 4 for frame f: the output posteriors of every column (core columns
+// copied from the compact state), hard decisions c_n = [L_qn < 0], and the
+// syndrome test.  Returns, identically in every thread of the block, nonzero
+// when H c != s.
 //   deg1_from_channel: no iteration ran, so degree-1 columns still hold the channel
 template <typename M>
 __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, const Frame<M> &fr,
@@ -411,9 +428,13 @@ __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, 
         const int kind = s.col_kind[c];
         const bool from_channel = kind == kColUnconnected || (kind == kColDegree1 && deg1_from_channel);
         const size_t base = (size_t)c * Z;
+        const float *core = kind == kColCore ? fr.post_core + (size_t)s.col_core[c] * Z : nullptr;
         for (int i = threadIdx.x; i < Z; i += blockDim.x) {
             float L;
-            if (from_channel) {
+            if (core) {
+                L = core[i];
+                fr.post[base + i] = L;
+            } else if (from_channel) {
                 L = fr.ch[base + i];
                 fr.post[base + i] = L;
             } else {
@@ -436,7 +457,7 @@ __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, 
                 const int4 en = ent[e];
                 int jj = i + en.y;
                 jj = jj >= Z ? jj - Z : jj;
-                par ^= hard[en.x + jj];
+                par ^= hard[(size_t)en.w * Z + jj];
             }
             fail |= (int)par;
         }
@@ -460,13 +481,14 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
     fr.ch = a.ch + (size_t)f * n;
     fr.syn = a.syn + (size_t)f * (size_t)a.m;
     fr.post = a.post + (size_t)f * n;
+    fr.post_core = a.post_core + (size_t)f * (size_t)a.core_cols * Z;
     fr.msg = static_cast<M *>(a.msgs) + (size_t)f * (size_t)a.msg_slots * stride;
 
     // Step 1: L_qn = channel LLR for every variable that carries state.
     for (int c = 0; c < s.nb; ++c) {
         if (s.col_kind[c] != kColCore) continue;
         const float *src = fr.ch + (size_t)c * Z;
-        float *dst = fr.post + (size_t)c * Z;
+        float *dst = fr.post_core + (size_t)s.col_core[c] * Z;
         for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
     }
     if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
@@ -551,6 +573,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const 
         a.ch = fd.ch;
         a.syn = fd.syn;
         a.post = fd.post;
+        a.post_core = fd.post_core;
         a.msgs = fd.msgs;
         a.hard = fd.hard;
         a.ok = fd.ok;
@@ -563,6 +586,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const 
         a.m = fd.m;
         a.nb = fd.nb;
         a.msg_slots = fd.msg_slots;
+        a.core_cols = fd.core_cols;
         a.slot_stride = fd.slot_stride;
         a.check_every = 0;
         a.iters_used = nullptr;
@@ -580,7 +604,8 @@ int sm_count_cached() {
 }
 
 template <typename M>
-int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &err) {
+int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &err,
+                 size_t window_bytes = 0, float hit_ratio = 0.0f) {
     const size_t smem = (size_t)a.image_words * sizeof(int32_t);
     auto kern = decode_kernel<M>;
     if (smem > 48 * 1024) {
@@ -597,8 +622,25 @@ int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &er
         return QCMET_ERR_CUDA;
     }
     const int grid = a.K < sms ? a.K : sms;
-    kern<<<grid, threads, smem, static_cast<cudaStream_t>(stream)>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    if (window_bytes > 0) {
+        // the core posteriors persist in L2; whatever misses the window streams
+        attr[0].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[0].val.accessPolicyWindow.base_ptr = a.post_core;
+        attr[0].val.accessPolicyWindow.num_bytes = window_bytes;
+        attr[0].val.accessPolicyWindow.hitRatio = hit_ratio;
+        attr[0].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[0].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("decode launch: ") + cudaGetErrorString(e);
         return QCMET_ERR_CUDA;
@@ -654,16 +696,19 @@ int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
 }
 
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
-                  std::string &err) {
+                  std::string &err, size_t window_bytes, float hit_ratio) {
     if (threads == 0) threads = kDefaultThreads;
     if (threads < 32 || threads > kDefaultThreads || threads % 32) {
         err = "threads_per_block must be a multiple of 32 in [32, 1024]";
         return QCMET_ERR_INVALID_ARG;
     }
     switch (msg_format) {
-        case QCMET_MSG_FP32: return launch_typed<float>(a, threads, stream, err);
-        case QCMET_MSG_FP16: return launch_typed<__half>(a, threads, stream, err);
-        case QCMET_MSG_BF16: return launch_typed<__nv_bfloat16>(a, threads, stream, err);
+        case QCMET_MSG_FP32:
+            return launch_typed<float>(a, threads, stream, err, window_bytes, hit_ratio);
+        case QCMET_MSG_FP16:
+            return launch_typed<__half>(a, threads, stream, err, window_bytes, hit_ratio);
+        case QCMET_MSG_BF16:
+            return launch_typed<__nv_bfloat16>(a, threads, stream, err, window_bytes, hit_ratio);
         default: err = "unknown message format"; return QCMET_ERR_INVALID_ARG;
     }
 }
@@ -723,10 +768,14 @@ int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_
               " bytes; qcmet_decode_noalloc reserves " + std::to_string(kNoAllocImageBytes);
         return QCMET_ERR_INVALID_ARG;
     }
-    const size_t need = (size_t)a.K * (size_t)a.msg_slots * (size_t)a.slot_stride * sizeof(float);
+    const size_t msg_bytes =
+        ((size_t)a.K * (size_t)a.msg_slots * (size_t)a.slot_stride * sizeof(float) + 255) &
+        ~size_t(255);
+    const size_t core_bytes = (size_t)a.K * (size_t)a.core_cols * (size_t)a.Z * sizeof(float);
+    const size_t need = msg_bytes + core_bytes;
     if (need > noalloc_capacity_bytes()) {
         err = "decoding these frames needs " + std::to_string(need) +
-              " bytes of message scratch; qcmet_decode_noalloc holds " +
+              " bytes of message and state scratch; qcmet_decode_noalloc holds " +
               std::to_string(noalloc_capacity_bytes()) + " (use fewer frames per call or qcmet_decode)";
         return QCMET_ERR_INVALID_ARG;
     }
@@ -735,8 +784,9 @@ int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_
     if (st) return st;
     char *p = static_cast<char *>(base);
     // The layer table is copied in every call: the array keeps whatever the
-    // previous call left there.  The messages need no clearing (the first
-    // iteration does not read them).
+    // previous call left there.  The messages and the core posteriors need no
+    // clearing (the first iteration does not read the messages; step 1 writes
+    // every core posterior before it is read).
     cudaError_t e = cudaMemcpyAsync(p, image_host, image_bytes, cudaMemcpyHostToDevice,
                                     static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) {
@@ -745,6 +795,7 @@ int launch_decode_noalloc(DecodeArgs a, const int32_t *image_host, size_t image_
     }
     a.image = reinterpret_cast<const int32_t *>(p);
     a.msgs = p + kNoAllocImageBytes;
+    a.post_core = reinterpret_cast<float *>(p + kNoAllocImageBytes + msg_bytes);
     return launch_typed<float>(a, kDefaultThreads, stream, err);
 }
 

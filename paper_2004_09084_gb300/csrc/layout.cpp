@@ -148,7 +148,12 @@ int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb
     std::vector<int32_t> slot(cells, -1);
     c.msg_slots = 0;
     c.degree1_columns = 0;
-    for (int32_t k = 0; k < nb; ++k) c.degree1_columns += c.col_degree[k] == 1;
+    c.core_cols = 0;
+    std::vector<int32_t> col_core(nb, -1);
+    for (int32_t k = 0; k < nb; ++k) {
+        c.degree1_columns += c.col_degree[k] == 1;
+        if (c.col_degree[k] > 1) col_core[k] = c.core_cols++;
+    }
     for (int32_t l = 0; l < mb; ++l)
         for (int32_t k = 0; k < nb; ++k) {
             const size_t i = (size_t)l * nb + k;
@@ -182,7 +187,8 @@ int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb
         for (int32_t k = 0; k < nb; ++k) {
             const size_t i = (size_t)r * nb + k;
             if (!c.base[i]) continue;
-            ents.push_back(DevEntry{k * Z, c.shifts[i], slot[i], k});
+            const int32_t vb = col_core[k] >= 0 ? col_core[k] * Z : k * Z;
+            ents.push_back(DevEntry{vb, c.shifts[i], slot[i], k});
             ++deg;
         }
         dr.degree = deg;
@@ -207,6 +213,11 @@ int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb
     im.n_zero_rows = (int32_t)c.zero_rows.size();
     for (int32_t r : c.zero_rows) w.push_back(r);
     pad4(w);
+    const int32_t off_col_core = (int32_t)w.size();
+    for (int32_t k = 0; k < nb; ++k) w.push_back(col_core[k]);
+    pad4(w);
+    w[kHdrOffColCore] = off_col_core;
+    w[kHdrCoreCols] = c.core_cols;
     w[kHdrOffLayerFirst] = im.off_layer_first;
     w[kHdrOffRows] = im.off_rows;
     w[kHdrOffEntries] = im.off_entries;

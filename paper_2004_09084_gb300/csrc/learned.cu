@@ -128,7 +128,7 @@ __device__ __forceinline__ void ms_check_forward(const LearnedArgs &a, const Lea
         const int4 en = ent[e];
         int j = i + en.y;
         j = j >= Z ? j - Z : j;
-        vv[e] = en.x + j;
+        vv[e] = en.w * Z + j;  // frame variable (column en.w)
         const float *src = en.z < 0 ? fv.ch : fv.post;
         const float lv = src[vv[e]];
         const float ro = (t > 0 && en.z >= 0) ? fv.msg[(size_t)en.z * stride + i] : 0.0f;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void ms_check_backward(const LearnedArgs &a, const Le
         const int4 en = ent[e];
         int j = i + en.y;
         j = j >= Z ? j - Z : j;
-        vv[e] = en.x + j;
+        vv[e] = en.w * Z + j;  // frame variable (column en.w)
         if (en.z < 0) {
             q[e] = fv.ch[vv[e]];
             gq[e] = 0.0f;

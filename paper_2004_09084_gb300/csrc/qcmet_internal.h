@@ -20,10 +20,11 @@ enum ColumnKind : int32_t {
 
 // One circulant of a base row as the layer kernel reads it.
 struct DevEntry {
-    int32_t var_base;  // c * Z: first variable of the block column
+    int32_t var_base;  // core column: cc * Z, its offset among the core posteriors
+                       // (cc = index among core columns); degree-1 column: c * Z
     int32_t shift;     // circulant shift a
     int32_t slot;      // message slot for core columns, -1 for a degree-1 column
-    int32_t col;       // base column c
+    int32_t col;       // base column c (frame variables c*Z .. c*Z + Z - 1)
 };
 
 // One scheduled base row.
@@ -42,10 +43,11 @@ struct DevRow {
 //   entries[n_entries] (DevEntry, 4 ints each)
 //   col_kind[nb]                         (padded to a multiple of 4)
 //   zero_rows[...]: base rows with no circulant (their checks test s_m = 0)
+//   col_core[nb]: index of a core column among the core columns, else -1 (padded)
 enum : int32_t {
     kHdrRows = 0, kHdrLayers, kHdrEntries, kHdrNb, kHdrZ, kHdrMb,
     kHdrOffLayerFirst, kHdrOffRows, kHdrOffEntries, kHdrOffColKind, kHdrOffZeroRows,
-    kHdrZeroRows, kHdrWords
+    kHdrZeroRows, kHdrOffColCore, kHdrCoreCols, kHdrPad0, kHdrPad1, kHdrWords
 };
 
 struct ScheduleImage {
@@ -93,6 +95,7 @@ struct Code {
     std::vector<int32_t> zero_rows;         // rows with no circulant
     int32_t circulants = 0;
     int32_t msg_slots = 0;
+    int32_t core_cols = 0;                  // columns of degree > 1
     int32_t degree1_columns = 0;
     int32_t max_row_degree = 0;
     ScheduleImage image;
@@ -105,6 +108,8 @@ struct Code {
     size_t msgs_bytes = 0;
     float *d_post = nullptr;      // posterior scratch when the caller passes no llr_post
     size_t post_bytes = 0;
+    float *d_core = nullptr;      // [K][core_cols][Z] posteriors of the core columns
+    size_t core_bytes = 0;
     // staging buffers of qcmet_decode_host
     void *d_io = nullptr;
     size_t io_bytes = 0;
@@ -132,7 +137,8 @@ inline size_t slot_stride(int32_t Z) { return (static_cast<size_t>(Z) + 15) & ~s
 struct DecodeArgs {
     const float *ch;         // [K][n]
     const uint8_t *syn;      // [K][m]
-    float *post;             // [K][n] posteriors (the caller's llr_post or scratch)
+    float *post;             // [K][n] posterior output (the caller's llr_post or scratch)
+    float *post_core;        // [K][core_cols*Z] posteriors of the core columns (decoder state)
     void *msgs;              // [K][msg_slots][slot_stride] messages
     uint8_t *hard;           // [K][n]
     uint8_t *ok;             // [K]
@@ -140,6 +146,7 @@ struct DecodeArgs {
     int32_t image_words;
     int32_t K, T, Z, n, m, nb;
     int32_t msg_slots;
+    int32_t core_cols;
     int64_t slot_stride;     // elements
     int32_t check_every;     // > 0: early termination test every check_every iterations
     int32_t *iters_used;     // [K] iterations each frame ran, or nullptr
@@ -154,6 +161,7 @@ struct BatchFrame {
     const float *ch;         // [n]
     const uint8_t *syn;      // [m]
     float *post;             // [n]
+    float *post_core;        // [core_cols * Z]
     uint8_t *hard;           // [n]
     uint8_t *ok;             // [1]
     void *msgs;              // [msg_slots][slot_stride] messages
@@ -162,7 +170,7 @@ struct BatchFrame {
     int32_t code_id;         // frames with equal code_id share the image
     int32_t Z, n, m, nb;
     int32_t msg_slots;
-    int32_t pad;
+    int32_t core_cols;
 };
 
 struct BatchArgs {
@@ -176,8 +184,10 @@ int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
                         int32_t max_image_words, void *stream, std::string &err);
 
 // Launch the fused decode kernel for one message format (decode.cu).
+// window_bytes > 0 attaches an L2 persisting access-policy window of that many
+// bytes, starting at a.post_core, with the given hit ratio, to the launch.
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
-                  std::string &err);
+                  std::string &err, size_t window_bytes = 0, float hit_ratio = 0.0f);
 
 // Launch the FP32 decode kernel with its messages and layer table in the
 // library's static device scratch (decode.cu): no device allocation.

@@ -292,6 +292,21 @@ def test_full_size_fixed_iterations_properties(q, full):
     np.testing.assert_array_equal(ok2, ok)
 
 
+def test_l2_persist_window_changes_no_result(q, full):
+    # the option only attaches an L2 access-policy window to the launch
+    code, fr = full
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d_llr = torch.from_numpy(fr.llr[:40]).cuda()
+    d_syn = torch.from_numpy(fr.syn[:40]).cuda()
+    h, p, ok = q.decode(qc, d_llr, d_syn, 6)
+    h2, p2, ok2 = q.decode(qc, d_llr, d_syn, 6, l2_persist=True)
+    torch.cuda.synchronize()
+    assert torch.equal(h, h2) and torch.equal(p, p2) and torch.equal(ok, ok2)
+    h3, p3, ok3 = q.decode_host(qc, fr.llr[:3], fr.syn[:3], 6, l2_persist=True)
+    np.testing.assert_array_equal(h3, h[:3].cpu().numpy())
+    np.testing.assert_array_equal(p3, p[:3].cpu().numpy())
+
+
 # --------------------------------------------------------------------------
 # Early termination (Discussion, Table tabearly)
 
