@@ -292,6 +292,19 @@ def test_full_size_fixed_iterations_properties(q, full):
     np.testing.assert_array_equal(ok2, ok)
 
 
+def test_block_size_does_not_change_results_at_full_size(q, full):
+    # one warp per frame against the default 1024 threads: per check the
+    # arithmetic is the same, so the results are identical
+    code, fr = full
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d_llr = torch.from_numpy(fr.llr[:6]).cuda()
+    d_syn = torch.from_numpy(fr.syn[:6]).cuda()
+    h, p, ok = q.decode(qc, d_llr, d_syn, 3, threads=1024)
+    h2, p2, ok2 = q.decode(qc, d_llr, d_syn, 3, threads=32)
+    torch.cuda.synchronize()
+    assert torch.equal(p, p2) and torch.equal(h, h2) and torch.equal(ok, ok2)
+
+
 def test_l2_persist_window_changes_no_result(q, full):
     # the option only attaches an L2 access-policy window to the launch
     code, fr = full
