@@ -488,7 +488,7 @@ def run_report(args):
                      w_offset=wo.detach().cpu().numpy())
         return 0
     if args.report == "batch":
-        # configs[4]: 192 codewords across rates 0.1/0.05/0.02 and lengths
+        # mixed batch: 192 codewords across rates 0.1/0.05/0.02 and lengths
         # 1e5 / 5e5 / 1e6 (Z = 1250 / 6250 / 12500) in one graph-captured launch
         plan = [(Zl, Kl) for Zl, Kl in ((1250, 22), (6250, 21), (12500, 21))]
         frames, bits, groups = [], 0, []

@@ -132,7 +132,8 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
 int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                   int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok,
                   const qcmet_decode_options *opts, void *stream, int32_t check_every = 0,
-                  int32_t *iters_used = nullptr) {
+                  int32_t *iters_used = nullptr, const float *w_scale = nullptr,
+                  const float *w_offset = nullptr) {
     int32_t fmt, threads;
     bool l2p = false;
     int st = check_options(opts, &fmt, &threads, &l2p);
@@ -196,8 +197,11 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     a.slot_stride = (int64_t)stride;
     a.check_every = check_every;
     a.iters_used = iters_used;
+    qcmet::CheckRule rule;
+    rule.w_scale = w_scale;
+    rule.w_offset = w_offset;
     std::string err;
-    st = qcmet::launch_decode(a, fmt, threads, stream, err, window, hit);
+    st = qcmet::launch_decode(a, fmt, threads, stream, err, window, hit, rule);
     if (st) return fail(st, err);
     return QCMET_OK;
 }
@@ -473,20 +477,11 @@ int qcmet_minsum_decode(const qcmet_code *code, const float *llr_ch, const uint8
         (w_offset && !aligned16(w_offset)))
         return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
     qcmet::Code &c = const_cast<qcmet_code *>(code)->c;
-    qcmet::LearnedArgs a;
-    int st = learned_setup(c, K, iterations, false, llr_post == nullptr, a);
-    if (st) return st;
-    if (llr_post) a.post = llr_post;
-    a.ch = llr_ch;
-    a.syn = syndrome;
-    a.w_scale = w_scale;
-    a.w_offset = w_offset;
-    a.hard = hard;
-    a.ok = ok;
-    std::string err;
-    st = qcmet::launch_learned_forward(a, false, stream, err);
-    if (st) return fail(st, err);
-    return QCMET_OK;
+    // the fused decode kernel with the min-sum rule (FP32 messages)
+    static const float kNoWeights[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (iterations == 0) w_scale = w_offset = kNoWeights;  // never read; selects the rule
+    return decode_device(c, llr_ch, syndrome, K, iterations, hard, llr_post, ok, nullptr, stream,
+                         0, nullptr, w_scale, w_offset);
 }
 
 int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,

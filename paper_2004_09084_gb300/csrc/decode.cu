@@ -384,6 +384,178 @@ __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int ch
     }
 }
 
+// ---- offset/scaled min-sum rows (the learned variant; not the paper's rule) ----
+//
+// |r_e| = max(scale * min_{k != e} |q_k| - offset, 0) with the sign of step 2;
+// wt = (scale for an edge to a core variable, scale for a degree-1 variable,
+// offset core, offset degree-1) of this row and iteration.  The gathers and
+// writes are those of the sum-product rows.
+constexpr float kNoOtherEdge = 30.0f;  // min over the empty set (a degree-1 check)
+#ifndef QCMET_BATCH_MINSUM
+#define QCMET_BATCH_MINSUM 1
+#endif
+
+template <typename M>
+__device__ __forceinline__ void scatter_minsum(const int4 &en, int i, float q, float mn,
+                                               unsigned par, const float4 &wt, const Frame<M> &fr,
+                                               int Z, size_t stride, bool last) {
+    const bool deg1 = en.z < 0;
+    if (deg1 && !last) return;
+    const float a_e = (deg1 ? wt.y : wt.x) * mn - (deg1 ? wt.w : wt.z);
+    const float mag = fmaxf(a_e, 0.0f);
+    const bool neg = ((par ^ (q < 0.0f ? 1u : 0u)) & 1u) != 0u;
+    float rn = neg ? -mag : mag;
+    int j = i + en.y;
+    j = j >= Z ? j - Z : j;
+    const int v = en.x + j;
+    if (!deg1) {
+        rn = Msg<M>::quantize(rn);
+        Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
+        fr.post_core[v] = q + rn;
+    } else {
+        fr.post[v] = q + rn;
+    }
+}
+
+// Rows of degree D <= 4, one thread per check (the gather of run_row).
+template <int D, typename M>
+__device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int check_base,
+                                               const Frame<M> &fr, int Z, size_t stride, bool first,
+                                               bool last, const float4 &wt) {
+    constexpr int U = QCMET_BATCH_MINSUM;
+    const int step = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
+        float lv[U][D], ro[U][D];
+        unsigned par[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = min(i0 + k * step, Z - 1);
+            par[k] = fr.syn[check_base + i] & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const int4 en = ent[e];
+                int j = i + en.y;
+                j = j >= Z ? j - Z : j;
+                const float *src = en.z < 0 ? fr.ch : fr.post_core;
+                lv[k][e] = src[en.x + j];
+                const bool has_old = !first && en.z >= 0;
+                ro[k][e] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + i) : 0.0f;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = i0 + k * step;
+            if (i >= Z) break;
+            float q[D];
+            unsigned p = par[k];
+            float m1 = INFINITY, m2 = INFINITY;
+            int i1 = -1;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                q[e] = lv[k][e] - ro[k][e];
+                p ^= q[e] < 0.0f ? 1u : 0u;
+                const float v = fabsf(q[e]);
+                if (v < m1) {
+                    m2 = m1;
+                    m1 = v;
+                    i1 = e;
+                } else if (v < m2) {
+                    m2 = v;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const float mn = D == 1 ? kNoOtherEdge : (e == i1 ? m2 : m1);
+                scatter_minsum<M>(ent[e], i, q[e], mn, p, wt, fr, Z, stride, last);
+            }
+        }
+    }
+}
+
+// Rows of degree 5..16: lanes l and l ^ 16 share a check (as run_row_pair);
+// each lane finds the two smallest |q| of its edges and takes the partner's
+// smallest by one shuffle.
+template <int D, typename M>
+__device__ __forceinline__ void run_row_pair_minsum(const int4 *__restrict__ ent, int check_base,
+                                                    const Frame<M> &fr, int Z, size_t stride,
+                                                    bool first, bool last, const float4 &wt) {
+    constexpr int E = (D + 1) / 2;
+    const int lane = threadIdx.x & 31;
+    const int part = lane >> 4;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int i0 = warp * 16; i0 < Z; i0 += nwarps * 16) {
+        const int i = i0 + (lane & 15);
+        const bool valid = i < Z;
+        float q[E];
+        unsigned par = (valid && part == 0) ? (fr.syn[check_base + i] & 1u) : 0u;
+        float m1 = INFINITY, m2 = INFINITY;
+        int i1 = -1;
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const int e = part * E + el;
+            q[el] = 0.0f;
+            if (valid && e < D) {
+                q[el] = gather_q<M>(ent[e], i, fr, Z, stride, first);
+                par ^= q[el] < 0.0f ? 1u : 0u;
+                const float v = fabsf(q[el]);
+                if (v < m1) {
+                    m2 = m1;
+                    m1 = v;
+                    i1 = el;
+                } else if (v < m2) {
+                    m2 = v;
+                }
+            }
+        }
+        const float om1 = __shfl_xor_sync(0xffffffffu, m1, 16);
+        par ^= __shfl_xor_sync(0xffffffffu, par, 16);
+        if (!valid) continue;
+        // excluding this lane's argmin: its next smallest or the partner's
+        // smallest; excluding any other edge of this lane: the overall smallest
+        const float ex1 = fminf(m2, om1);
+        const float exo = fminf(m1, om1);
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const int e = part * E + el;
+            if (e < D)
+                scatter_minsum<M>(ent[e], i, q[el], el == i1 ? ex1 : exo, par, wt, fr, Z, stride,
+                                  last);
+        }
+    }
+}
+
+template <typename M>
+__device__ __forceinline__ void dispatch_row_minsum(int degree, const int4 *ent, int check_base,
+                                                    const Frame<M> &fr, int Z, size_t stride,
+                                                    bool first, bool last, const float4 &wt) {
+    switch (degree) {
+#define QCMET_ROW_CASE(DD) \
+    case DD: run_row_minsum<DD, M>(ent, check_base, fr, Z, stride, first, last, wt); break;
+#define QCMET_PAIR_CASE(DD) \
+    case DD: run_row_pair_minsum<DD, M>(ent, check_base, fr, Z, stride, first, last, wt); break;
+        QCMET_ROW_CASE(1)
+        QCMET_ROW_CASE(2)
+        QCMET_ROW_CASE(3)
+        QCMET_ROW_CASE(4)
+        QCMET_PAIR_CASE(5)
+        QCMET_PAIR_CASE(6)
+        QCMET_PAIR_CASE(7)
+        QCMET_PAIR_CASE(8)
+        QCMET_PAIR_CASE(9)
+        QCMET_PAIR_CASE(10)
+        QCMET_PAIR_CASE(11)
+        QCMET_PAIR_CASE(12)
+        QCMET_PAIR_CASE(13)
+        QCMET_PAIR_CASE(14)
+        QCMET_PAIR_CASE(15)
+        QCMET_PAIR_CASE(16)
+#undef QCMET_ROW_CASE
+#undef QCMET_PAIR_CASE
+        default: break;
+    }
+}
+
 // Warp 0 prefetches into L2 what scheduled row `j` of iteration `t` will read.
 template <typename M>
 __device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a, int f, int j,
@@ -471,8 +643,11 @@ __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, 
 
 // Decode frame f of `a` (steps 1-4) with the schedule `s` already in shared
 // memory.  Called by every thread of the block.
-template <typename M>
-__device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArgs &a, int f) {
+enum : int { kRuleSumProduct = 0, kRuleMinSum = 1 };
+
+template <typename M, int R>
+__device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArgs &a, int f,
+                                                 const float *w_scale, const float *w_offset) {
     const int Z = s.Z;
     const size_t n = (size_t)a.n;
     const size_t stride = (size_t)a.slot_stride;
@@ -512,7 +687,15 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
                     else if (!final_iter) prefetch_row<M>(s, a, f, 0, t + 1);
                 }
                 const int4 row = s.rows[j];
-                dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
+                if constexpr (R == kRuleSumProduct) {
+                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
+                } else {
+                    const size_t w = ((size_t)t * s.mb + (size_t)row.w) * 2;
+                    const float4 wt = make_float4(__ldg(w_scale + w), __ldg(w_scale + w + 1),
+                                                  __ldg(w_offset + w), __ldg(w_offset + w + 1));
+                    dispatch_row_minsum<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first,
+                                           check, wt);
+                }
             }
             __syncthreads();
         }
@@ -532,8 +715,10 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
     __syncthreads();
 }
 
-template <typename M>
-__global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a) {
+template <typename M, int R>
+__global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a,
+                                                                    const float *w_scale,
+                                                                    const float *w_offset) {
     extern __shared__ int4 smem_i4[];
     int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
     {
@@ -542,7 +727,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
     }
     __syncthreads();
     const Sched s = make_sched(sw);
-    for (int f = blockIdx.x; f < a.K; f += gridDim.x) decode_one_frame<M>(s, a, f);
+    for (int f = blockIdx.x; f < a.K; f += gridDim.x) decode_one_frame<M, R>(s, a, f, w_scale, w_offset);
 }
 
 // Mixed batch: frames of several codes in one launch.  Persistent CTAs take
@@ -590,7 +775,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const 
         a.slot_stride = fd.slot_stride;
         a.check_every = 0;
         a.iters_used = nullptr;
-        decode_one_frame<M>(s, a, 0);
+        decode_one_frame<M, kRuleSumProduct>(s, a, 0, nullptr, nullptr);
     }
 }
 
@@ -603,11 +788,12 @@ int sm_count_cached() {
     return count[dev];
 }
 
-template <typename M>
+template <typename M, int R = kRuleSumProduct>
 int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &err,
-                 size_t window_bytes = 0, float hit_ratio = 0.0f) {
+                 size_t window_bytes = 0, float hit_ratio = 0.0f,
+                 const CheckRule &rule = CheckRule()) {
     const size_t smem = (size_t)a.image_words * sizeof(int32_t);
-    auto kern = decode_kernel<M>;
+    auto kern = decode_kernel<M, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -639,7 +825,7 @@ int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &er
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, a, rule.w_scale, rule.w_offset);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         err = std::string("decode launch: ") + cudaGetErrorString(e);
@@ -696,11 +882,19 @@ int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
 }
 
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
-                  std::string &err, size_t window_bytes, float hit_ratio) {
+                  std::string &err, size_t window_bytes, float hit_ratio, const CheckRule &rule) {
     if (threads == 0) threads = kDefaultThreads;
     if (threads < 32 || threads > kDefaultThreads || threads % 32) {
         err = "threads_per_block must be a multiple of 32 in [32, 1024]";
         return QCMET_ERR_INVALID_ARG;
+    }
+    if (rule.w_scale) {
+        if (msg_format != QCMET_MSG_FP32) {
+            err = "the min-sum rule keeps FP32 messages";
+            return QCMET_ERR_INVALID_ARG;
+        }
+        return launch_typed<float, kRuleMinSum>(a, threads, stream, err, window_bytes, hit_ratio,
+                                                rule);
     }
     switch (msg_format) {
         case QCMET_MSG_FP32:

@@ -152,6 +152,14 @@ struct DecodeArgs {
     int32_t *iters_used;     // [K] iterations each frame ran, or nullptr
 };
 
+// Check-node rule of the fused decode kernel: the paper's sum-product rule, or
+// offset/scaled min-sum with weights [T][mb][2] (FP32, device; the learned
+// variant).
+struct CheckRule {
+    const float *w_scale = nullptr;   // nullptr: sum-product
+    const float *w_offset = nullptr;
+};
+
 int launch_learned_forward(const LearnedArgs &a, bool train, void *stream, std::string &err);
 int launch_learned_backward(const LearnedArgs &a, void *stream, std::string &err);
 
@@ -187,7 +195,8 @@ int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
 // window_bytes > 0 attaches an L2 persisting access-policy window of that many
 // bytes, starting at a.post_core, with the given hit ratio, to the launch.
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
-                  std::string &err, size_t window_bytes = 0, float hit_ratio = 0.0f);
+                  std::string &err, size_t window_bytes = 0, float hit_ratio = 0.0f,
+                  const CheckRule &rule = CheckRule());
 
 // Launch the FP32 decode kernel with its messages and layer table in the
 // library's static device scratch (decode.cu): no device allocation.
