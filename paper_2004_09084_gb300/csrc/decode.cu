@@ -586,14 +586,12 @@ __device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a
     }
 }
 
-// Step 4 for frame f: the output posteriors of every column (core columns
-// copied from the compact state), hard decisions c_n = [L_qn < 0], and the
-// syndrome test.  Returns, identically in every thread of the block, nonzero
-// when H c != s.
+// Step 4 outputs for frame f: the posterior of every column (core columns
+// copied from the compact state) and the hard decisions c_n = [L_qn < 0].
 //   deg1_from_channel: no iteration ran, so degree-1 columns still hold the channel
 template <typename M>
-__device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, const Frame<M> &fr,
-                                       int f, bool deg1_from_channel) {
+__device__ __noinline__ void write_outputs(const Sched &s, const DecodeArgs &a, const Frame<M> &fr,
+                                           int f, bool deg1_from_channel) {
     const int Z = s.Z;
     const size_t n = (size_t)a.n;
     for (int c = 0; c < s.nb; ++c) {
@@ -615,30 +613,91 @@ __device__ __noinline__ int finalize_frame(const Sched &s, const DecodeArgs &a, 
             a.hard[(size_t)f * n + base + i] = L < 0.0f ? 1 : 0;
         }
     }
-    __syncthreads();
+}
 
-    // Syndrome test: ok = [H c = s].
-    const uint8_t *hard = a.hard + (size_t)f * n;
-    int fail = 0;
+// Nonzero when some check of the row (rows of degree D <= 4, one thread per
+// check) has s_m XOR (XOR of its variables' hard decisions) = 1.  The hard
+// decision [L < 0] is taken from the posteriors directly: the compact core
+// state, and llr_post for degree-1 columns (written in every tested
+// iteration).  Loads of U checks are issued together, as in run_row.
+template <int D, typename M>
+__device__ __forceinline__ int row_fails(const int4 *__restrict__ ent, int check_base,
+                                         const Frame<M> &fr, int Z) {
+    constexpr int U = 2;
+    const int step = blockDim.x;
+    for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
+        float lv[U][D];
+        unsigned par[U];
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const int i = min(i0 + k * step, Z - 1);
+            par[k] = fr.syn[check_base + i] & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const int4 en = ent[e];
+                int j = i + en.y;
+                j = j >= Z ? j - Z : j;
+                const float *src = en.z < 0 ? fr.post : fr.post_core;
+                lv[k][e] = src[en.x + j];
+            }
+        }
+        unsigned bad = 0u;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            unsigned p = par[k];
+#pragma unroll
+            for (int e = 0; e < D; ++e) p ^= lv[k][e] < 0.0f ? 1u : 0u;
+            bad |= (i0 + k * step < Z) ? p : 0u;
+        }
+        if (bad) return 1;
+    }
+    return 0;
+}
+
+template <typename M>
+__device__ __forceinline__ int row_fails_any(const int4 *__restrict__ ent, int degree,
+                                             int check_base, const Frame<M> &fr, int Z) {
+    for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+        unsigned p = fr.syn[check_base + i] & 1u;
+        for (int e = 0; e < degree; ++e) {
+            const int4 en = ent[e];
+            int j = i + en.y;
+            j = j >= Z ? j - Z : j;
+            const float *src = en.z < 0 ? fr.post : fr.post_core;
+            p ^= src[en.x + j] < 0.0f ? 1u : 0u;
+        }
+        if (p) return 1;
+    }
+    return 0;
+}
+
+// The syndrome test H c = s on the current posteriors.  Returns, identically
+// in every thread of the block, nonzero when it fails.  A frame that has not
+// converged fails in its first rows, so the block stops at the first row with
+// a failing check (one barrier-with-OR per row): a failed test costs about one
+// row, a passed one a read of every edge's posterior.
+template <typename M>
+__device__ __noinline__ int syndrome_fails(const Sched s, const Frame<M> fr) {
+    const int Z = s.Z;
+    int bad = 0;
+    for (int zr = 0; zr < s.n_zero_rows; ++zr) {
+        const size_t cb = (size_t)s.zero_rows[zr] * Z;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x) bad |= fr.syn[cb + i] & 1;
+    }
+    if (__syncthreads_or(bad)) return 1;
     for (int j = 0; j < s.n_rows; ++j) {
         const int4 row = s.rows[j];
         const int4 *ent = s.entries + row.x;
-        for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-            unsigned par = fr.syn[row.z + i] & 1u;
-            for (int e = 0; e < row.y; ++e) {
-                const int4 en = ent[e];
-                int jj = i + en.y;
-                jj = jj >= Z ? jj - Z : jj;
-                par ^= hard[(size_t)en.w * Z + jj];
-            }
-            fail |= (int)par;
+        switch (row.y) {
+            case 1: bad = row_fails<1, M>(ent, row.z, fr, Z); break;
+            case 2: bad = row_fails<2, M>(ent, row.z, fr, Z); break;
+            case 3: bad = row_fails<3, M>(ent, row.z, fr, Z); break;
+            case 4: bad = row_fails<4, M>(ent, row.z, fr, Z); break;
+            default: bad = row_fails_any<M>(ent, row.y, row.z, fr, Z); break;
         }
+        if (__syncthreads_or(bad)) return 1;
     }
-    for (int zr = 0; zr < s.n_zero_rows; ++zr) {
-        const size_t cb = (size_t)s.zero_rows[zr] * Z;
-        for (int i = threadIdx.x; i < Z; i += blockDim.x) fail |= fr.syn[cb + i] & 1;
-    }
-    return __syncthreads_or(fail);
+    return 0;
 }
 
 // Decode frame f of `a` (steps 1-4) with the schedule `s` already in shared
@@ -675,7 +734,7 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
     // Those iterations, like the last one, also write the posteriors of the
     // degree-1 columns, which the test needs.
     int t_stop = T;
-    bool tested = false;
+    int fail = 1;
     for (int t = 0; t < T; ++t) {
         const bool first = t == 0;
         const bool final_iter = t == T - 1;
@@ -699,15 +758,20 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
             }
             __syncthreads();
         }
-        if (a.check_every > 0 && check && !final_iter &&
-            finalize_frame<M>(s, a, fr, f, false) == 0) {
-            t_stop = t + 1;
-            tested = true;
-            break;
+        if (check) {
+            fail = syndrome_fails<M>(s, fr);
+            if (!fail && a.check_every > 0) {
+                t_stop = t + 1;
+                break;
+            }
         }
     }
 
-    const int fail = tested ? 0 : finalize_frame<M>(s, a, fr, f, T == 0);
+    write_outputs<M>(s, a, fr, f, T == 0);
+    if (T == 0) {
+        __syncthreads();
+        fail = syndrome_fails<M>(s, fr);
+    }
     if (threadIdx.x == 0) {
         a.ok[f] = fail ? 0 : 1;
         if (a.iters_used) a.iters_used[f] = t_stop;
