@@ -143,7 +143,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline)
 
-def oracle_sample(code, cores: int, iters: int = 2):
+def oracle_sample(code, cores: int, iters: int = 20):
     """Time the FP64 oracle on `cores` frames x `iters` iterations; returns (Mbit/s, seconds, desc)."""
     import oracle
     fr = synth.make_frames(code, cores, SNR, first=10_000)

@@ -22,9 +22,9 @@
 //  * Degree-1 variables (a base column with a single circulant) keep no state:
 //    for them L_qn - L_rmn(old) equals the channel LLR exactly, so q is read
 //    from the channel array and L_qn is written once, in the last iteration.
-//  * While a row is processed, warp 0 issues bulk L2 prefetches of the next
-//    row's message slots, posterior columns, channel columns and syndrome
-//    bits, so HBM streams ahead of the layer barrier.
+//  * No software prefetch: bulk L2 prefetches of the next row's operands
+//    were evicted before use often enough to add about a third to the DRAM
+//    reads, and the decode ran faster without them.
 //  * The check rule is evaluated in the tanh-product form
 //    |r_e| = 2 atanh(prod_{k != e} tanh(|q_k|/2)), which equals
 //    Phi(sum_{k != e} Phi(|q_k|)) (Methods, step 2).  With u_k = exp(-|q_k|),
@@ -59,6 +59,25 @@ constexpr float kLog2e = 1.442695040888963407f;
 #endif
 constexpr int kDefaultThreads = QCMET_THREADS;
 
+// ---- transcendentals --------------------------------------------------------
+//
+// The check rule takes exp2 of arguments in [-30 log2(e), 0] and log2 of
+// alpha >= 1 and beta >= exp(-30) (beta = 0 only for a check of degree 1,
+// whose log is -inf and whose magnitude clips to 30).  No argument or result
+// is subnormal, so the flush-to-zero forms of the hardware approximations
+// return what the non-flushing ones do, without the subnormal handling.
+__device__ __forceinline__ float ex2_ftz(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_ftz(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---- message storage formats ---------------------------------------------
 
 template <typename M>
@@ -92,26 +111,6 @@ struct Msg<__nv_bfloat16> {
         *p = __float2bfloat16_rn(x);
     }
 };
-
-// ---- L2 prefetch -----------------------------------------------------------
-
-// Prefetch bytes [off, off + len) of a buffer that starts 16-byte aligned and
-// holds `total` bytes.  The range is widened to 16-byte boundaries and clipped
-// to the buffer, as cp.async.bulk requires aligned addresses and sizes.
-__device__ __forceinline__ void prefetch_l2(const void *buf, size_t total, size_t off, size_t len) {
-    size_t lo = off & ~size_t(15);
-    size_t hi = (off + len + 15) & ~size_t(15);
-    const size_t cap = total & ~size_t(15);
-    if (hi > cap) hi = cap;
-    const char *p = static_cast<const char *>(buf);
-    while (lo < hi) {
-        const size_t chunk = (hi - lo) > 32768 ? 32768 : (hi - lo);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + lo),
-                     "r"(static_cast<unsigned>(chunk))
-                     : "memory");
-        lo += chunk;
-    }
-}
 
 // ---- shared-memory view of the schedule ------------------------------------
 
@@ -224,7 +223,7 @@ __device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float 
                                           unsigned par, const Frame<M> &fr, int Z, size_t stride,
                                           bool last) {
     if (en.z < 0 && !last) return;
-    float mag = kLn2 * (__log2f(a) - __log2f(b));
+    float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
     mag = fminf(fmaxf(mag, kClipMin), kClipMax);
     const bool neg = ((par ^ (q < 0.0f ? 1u : 0u)) & 1u) != 0u;
     float rn = neg ? -mag : mag;
@@ -241,7 +240,7 @@ __device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float 
 }
 
 __device__ __forceinline__ float u_of(float q) {
-    return exp2f(-kLog2e * fminf(fabsf(q), kClipMax));
+    return ex2_ftz(-kLog2e * fminf(fabsf(q), kClipMax));
 }
 
 // Rows of degree D <= 4: one thread per check.  Each thread first gathers the
@@ -556,36 +555,6 @@ __device__ __forceinline__ void dispatch_row_minsum(int degree, const int4 *ent,
     }
 }
 
-// Warp 0 prefetches into L2 what scheduled row `j` of iteration `t` will read.
-template <typename M>
-__device__ __forceinline__ void prefetch_row(const Sched &s, const DecodeArgs &a, int f, int j,
-                                             int t) {
-    const int lane = threadIdx.x;  // only warp 0 calls this
-    const int4 row = s.rows[j];
-    const size_t Z = (size_t)s.Z;
-    const size_t n = (size_t)a.n;
-    const size_t fl_bytes = (size_t)a.K * n * sizeof(float);
-    const size_t nc = (size_t)a.core_cols * Z;
-    if (lane < row.y) {
-        const int4 en = s.entries[row.x + lane];
-        if (en.z >= 0) {
-            if (t > 0) {
-                const M *slot = static_cast<const M *>(a.msgs) +
-                                ((size_t)f * a.msg_slots + (size_t)en.z) * (size_t)a.slot_stride;
-                // the slot stride is a multiple of 16 elements: the widened range stays inside it
-                prefetch_l2(slot, ((Z * sizeof(M)) + 15) & ~size_t(15), 0, Z * sizeof(M));
-            }
-            prefetch_l2(a.post_core, (size_t)a.K * nc * sizeof(float),
-                        ((size_t)f * nc + (size_t)en.x) * sizeof(float), Z * sizeof(float));
-        } else {
-            prefetch_l2(a.ch, fl_bytes, ((size_t)f * n + (size_t)en.x) * sizeof(float),
-                        Z * sizeof(float));
-        }
-    } else if (lane == 31) {
-        prefetch_l2(a.syn, (size_t)a.K * (size_t)a.m, (size_t)f * a.m + (size_t)row.z, Z);
-    }
-}
-
 // Step 4 outputs for frame f: the posterior of every column (core columns
 // copied from the compact state) and the hard decisions c_n = [L_qn < 0].
 //   deg1_from_channel: no iteration ran, so degree-1 columns still hold the channel
@@ -725,7 +694,6 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
         float *dst = fr.post_core + (size_t)s.col_core[c] * Z;
         for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
     }
-    if (T > 0 && s.n_rows > 0 && threadIdx.x < 32) prefetch_row<M>(s, a, f, 0, 0);
     __syncthreads();
 
     // Steps 2-3 over T iterations x layers.  With early termination
@@ -741,10 +709,6 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
         const bool check = final_iter || (a.check_every > 0 && (t + 1) % a.check_every == 0);
         for (int layer = 0; layer < s.n_layers; ++layer) {
             for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
-                if (threadIdx.x < 32) {
-                    if (j + 1 < s.n_rows) prefetch_row<M>(s, a, f, j + 1, t);
-                    else if (!final_iter) prefetch_row<M>(s, a, f, 0, t + 1);
-                }
                 const int4 row = s.rows[j];
                 if constexpr (R == kRuleSumProduct) {
                     dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
