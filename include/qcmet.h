@@ -227,11 +227,13 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
 /*
  * Learned offset/scaled min-sum (not part of the paper's method; a variant of
  * its layered decoder, Methods steps 1-4, whose check rule of step 2 becomes)
- *   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * max(w_scale[t][l][type_e] *
- *         min_{k != e} |q_k| - w_offset[t][l][type_e], 0)
+ *   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * min(max(a_e, 0), 30),
+ *   a_e = w_scale[t][l][type_e] * min_{k != e} |q_k| - w_offset[t][l][type_e]
  * for iteration t, base row l, and edge type 0 (edge to a variable of degree
- * > 1) or 1 (edge to a degree-1 variable).  Weights are device FP32 arrays of
- * shape [iterations][mb][2], row-major.
+ * > 1) or 1 (edge to a degree-1 variable).  The clip at 30 is the one the
+ * sum-product rule uses; without it unscaled min-sum can grow posteriors past
+ * the FP32 range.  Weights are device FP32 arrays of shape [iterations][mb][2],
+ * row-major.
  *
  * qcmet_minsum_decode: decode with given weights; outputs as qcmet_decode
  *   (FP32 messages, llr_post may be NULL).

@@ -148,8 +148,10 @@ static void check_tanh(int d, const double *q, int s, double *r)
     }
 }
 
-/* Offset/scaled min-sum: |r| = max(w_scale * min_{k != j} |q_k| - w_offset, 0),
- * sign as in step 2.  (Learned variant; not part of the paper's method.) */
+/* Offset/scaled min-sum: |r| = min(max(w_scale * min_{k != j} |q_k| - w_offset, 0), 30),
+ * sign as in step 2.  (Learned variant; not part of the paper's method.  The
+ * upper clip is the one the sum-product rule uses: without it, unscaled
+ * min-sum can grow posteriors geometrically past the FP32 range.) */
 static void check_minsum(int d, const double *q, int s, const double *w_scale,
                          const double *w_offset, double *r)
 {
@@ -165,6 +167,7 @@ static void check_minsum(int d, const double *q, int s, const double *w_scale,
         if (d == 1) mn = ORACLE_CLIP_MAX;
         double mag = w_scale[j] * mn - w_offset[j];
         if (mag < 0.0) mag = 0.0;
+        if (mag > ORACLE_CLIP_MAX) mag = ORACLE_CLIP_MAX;
         r[j] = (s ? -1.0 : 1.0) * sign * mag;
     }
 }
@@ -474,7 +477,7 @@ int oracle_decode(int mb, int nb, int Z, const int8_t *base, const int32_t *shif
 /* paper's method; the training target of the learned variant).           */
 /*                                                                        */
 /* Check rule (for the edge e that receives the message):                  */
-/*   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * max(a_e, 0),               */
+/*   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * min(max(a_e, 0), 30),      */
 /*   a_e = w_scale[t][l][type_e] * min_{k != e} |q_k| - w_offset[t][l][type_e]
 /* The rest of the layered update is Methods step 3.  Loss: the mean over   */
 /* iterations t and variables n of the binary cross-entropy of the bit     */
@@ -558,7 +561,8 @@ static int train_frame(const graph_t *g, int T, const float *llr_ch, const uint8
                     minsum_parts(d, q, j, &sg, &mn, &arg);
                     const size_t wi = ((size_t)t * mb + l) * 2 + g->circ_type[k];
                     double a = ws[wi] * mn - wo[wi];
-                    const double r = ssign * sg * (a > 0.0 ? a : 0.0);
+                    const double mag = a <= 0.0 ? 0.0 : (a >= ORACLE_CLIP_MAX ? ORACLE_CLIP_MAX : a);
+                    const double r = ssign * sg * mag;
                     Lr[(size_t)k * Z + i] = r;
                     Lq[v[j]] = q[j] + r;
                 }
@@ -599,7 +603,8 @@ static int train_frame(const graph_t *g, int T, const float *llr_ch, const uint8
                     minsum_parts(d, q, j, &sg, &mn, &arg);
                     const size_t wi = ((size_t)t * mb + l) * 2 + g->circ_type[k];
                     const double a = ws[wi] * mn - wo[wi];
-                    if (a <= 0.0) continue;    /* max(a, 0) inactive: no gradient */
+                    /* outside (0, 30) the clip holds |r| constant: no gradient */
+                    if (a <= 0.0 || a >= ORACLE_CLIP_MAX) continue;
                     const double s = ssign * sg;
                     gs[wi] += gr[j] * s * mn;
                     go[wi] += -gr[j] * s;

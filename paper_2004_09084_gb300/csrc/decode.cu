@@ -385,7 +385,8 @@ __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int ch
 
 // ---- offset/scaled min-sum rows (the learned variant; not the paper's rule) ----
 //
-// |r_e| = max(scale * min_{k != e} |q_k| - offset, 0) with the sign of step 2;
+// |r_e| = min(max(scale * min_{k != e} |q_k| - offset, 0), 30) with the sign of
+// step 2 (the upper clip is the sum-product rule's);
 // wt = (scale for an edge to a core variable, scale for a degree-1 variable,
 // offset core, offset degree-1) of this row and iteration.  The gathers and
 // writes are those of the sum-product rows.
@@ -401,7 +402,7 @@ __device__ __forceinline__ void scatter_minsum(const int4 &en, int i, float q, f
     const bool deg1 = en.z < 0;
     if (deg1 && !last) return;
     const float a_e = (deg1 ? wt.y : wt.x) * mn - (deg1 ? wt.w : wt.z);
-    const float mag = fmaxf(a_e, 0.0f);
+    const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
     const bool neg = ((par ^ (q < 0.0f ? 1u : 0u)) & 1u) != 0u;
     float rn = neg ? -mag : mag;
     int j = i + en.y;

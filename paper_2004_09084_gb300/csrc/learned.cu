@@ -3,7 +3,7 @@
 //
 // Not part of arXiv 2004.09084's method: a variant of its layered decoder
 // (Methods, steps 1-4) in which the check rule of step 2 becomes
-//   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * max(a_e, 0),
+//   r_e = (-1)^{s_m} prod_{k != e} sgn(q_k) * min(max(a_e, 0), 30),
 //   a_e = w_scale[t][l][type_e] * min_{k != e} |q_k| - w_offset[t][l][type_e],
 // with one scale and one offset per (iteration t, base row l, edge type);
 // type 0 marks an edge to a variable of degree > 1, type 1 an edge to a
@@ -31,7 +31,7 @@ namespace qcmet {
 namespace {
 
 constexpr int kThreads = 512;
-constexpr float kNoOther = 30.0f;  // min over an empty set (degree-1 check), as in the BP clip
+constexpr float kNoOther = 30.0f;  // the message clip; also min over an empty set (degree-1 check)
 
 struct LearnedView {
     int32_t n_rows, n_layers, nb, Z, mb, core_cols;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void ms_check_forward(const LearnedArgs &a, const Lea
         if (D == 1) mn = kNoOther;
         const float a_e = (deg1 ? ws1 : ws0) * mn - (deg1 ? wo1 : wo0);
         const bool neg = ((negs ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
-        const float mag = fmaxf(a_e, 0.0f);
+        const float mag = fminf(fmaxf(a_e, 0.0f), kNoOther);
         const float r = neg ? -mag : mag;
         const float L = q[e] + r;
         if (!deg1) {
@@ -358,11 +358,11 @@ __device__ __forceinline__ void ms_check_backward(const LearnedArgs &a, const Le
         const float sg = neg ? -1.0f : 1.0f;
         if (deg1) {
             // L_qn^(t) = channel + r: its loss term is the message's only use
-            const float r = sg * fmaxf(a_e, 0.0f);
+            const float r = sg * fminf(fmaxf(a_e, 0.0f), kNoOther);
             const float sx = fv.x[vv[e]] ? -1.0f : 1.0f;
             gr[e] = scale * (-sx) * sigmoidf(-sx * (q[e] + r));
         }
-        if (a_e <= 0.0f) continue;
+        if (a_e <= 0.0f || a_e >= kNoOther) continue;  // the clip holds |r| constant
         acc[deg1 ? 1 : 0] += gr[e] * sg * mn;   // d/d w_scale
         acc[deg1 ? 3 : 2] += -gr[e] * sg;       // d/d w_offset
         if (arg >= 0) {

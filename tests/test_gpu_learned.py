@@ -105,6 +105,62 @@ def test_loss_and_gradient_match_the_oracle(q, learned, Z, K, T, bar):
         assert rel <= bar and cos >= 0.999, (rel, cos)
 
 
+def test_message_clip_matches_the_oracle(q, learned):
+    # confident correct core LLRs (50) and confident wrong degree-1 LLRs (45):
+    # messages sit at the clip |r| = 30 in both directions; decode, loss and
+    # gradient follow the oracle, and nothing overflows
+    code = synth.make_code("0.1", 64)
+    fr = synth.make_frames(code, 4, 0.3)
+    deg = np.repeat(code.base.sum(axis=0), code.Z)
+    sx = 1.0 - 2.0 * fr.x
+    llr = np.where(deg > 1, 50.0 * sx, -45.0 * sx).astype(np.float32)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    T = 2
+    ws = np.full((T, code.mb, 2), 1.0, np.float32)
+    wo = np.full((T, code.mb, 2), 0.125, np.float32)
+    d_llr, d_syn = torch.from_numpy(llr).cuda(), torch.from_numpy(fr.syn).cuda()
+    h, p, ok = learned.decode(qc, d_llr, d_syn, torch.from_numpy(ws).cuda(), torch.from_numpy(wo).cuda())
+    torch.cuda.synchronize()
+    _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, llr, fr.syn, T, rule=oracle.RULE_MINSUM,
+                             w_scale=ws.astype(np.float64), w_offset=wo.astype(np.float64))
+    assert np.abs(rp).max() > 100.0              # large posteriors: the clip is active
+    assert rel_err(p.cpu().numpy(), rp).max() <= 1e-5
+    tws = torch.from_numpy(ws).cuda().requires_grad_()
+    two = torch.from_numpy(wo).cuda().requires_grad_()
+    loss = learned.minsum_loss(tws, two, qc, d_llr, d_syn, torch.from_numpy(fr.x).cuda())
+    loss.sum().backward()
+    torch.cuda.synchronize()
+    rl, rgs, rgo = oracle.minsum_train(code.base, code.shifts, code.Z, llr, fr.syn, fr.x, T,
+                                       ws.astype(np.float64), wo.astype(np.float64))
+    np.testing.assert_allclose(loss.detach().cpu().numpy(), rl, rtol=1e-4)
+    for g, rg in ((tws.grad, rgs), (two.grad, rgo)):
+        g = g.cpu().numpy().astype(np.float64).ravel()
+        assert np.all(np.isfinite(g))
+        rel = np.linalg.norm(g - rg.ravel()) / np.linalg.norm(rg)
+        assert rel <= 2e-3, rel
+
+
+def test_thirty_iterations_stay_finite(q, learned):
+    # The clip keeps the forward finite even for unscaled min-sum.  The exact
+    # gradient of 30 unrolled unscaled iterations is itself beyond the FP32
+    # range here (the FP64 oracle gives |dL/dw| ~ 1e42 at scale 1, ~1e13 at
+    # 0.5 and ~1e-3 at 0.25 on the Z = 64 code), so training starts from small
+    # scales; from scale 0.25 the FP32 backward stays finite.
+    code = synth.make_code("0.1", 2500)
+    fr = synth.make_frames(code, 4, 0.161)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d = dict(llr=torch.from_numpy(fr.llr).cuda(), syn=torch.from_numpy(fr.syn).cuda(),
+             bits=torch.from_numpy(fr.x).cuda())
+    ws, wo = learned.init_weights(qc, 30)
+    _, p, _ = learned.decode(qc, d["llr"], d["syn"], ws, wo)
+    assert bool(torch.isfinite(p).all())
+    ws, wo = learned.init_weights(qc, 30, scale=0.25)
+    ws.requires_grad_()
+    wo.requires_grad_()
+    learned.minsum_loss(ws, wo, qc, d["llr"], d["syn"], d["bits"]).mean().backward()
+    assert bool(torch.isfinite(ws.grad).all()) and bool(torch.isfinite(wo.grad).all())
+
+
 def test_autograd_mean_scales_the_gradient(q, learned):
     code = synth.make_code("0.1", 64)
     fr = synth.make_frames(code, 4, 0.2)

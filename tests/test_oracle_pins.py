@@ -307,7 +307,7 @@ def test_minsum_with_unit_weights_is_plain_minsum():
                 for j in range(len(vs)):
                     o = np.delete(q, j)
                     r[j] = (-1.0 if fr.syn[k, mrow] else 1.0) * np.prod(np.where(o < 0, -1.0, 1.0)) \
-                        * np.min(np.abs(o))
+                        * min(np.min(np.abs(o)), 30.0)
                 R[mrow, vs] = r
                 L[vs] = q + r
         np.testing.assert_allclose(post[k], L, rtol=1e-12, atol=1e-12)
@@ -327,6 +327,26 @@ def test_minsum_offset_and_scale():
     # edge 1: others (2, 0.5): sign +1 * -1 = -1, mag 0.125
     # edge 2: others (2, -3): sign -1 * -1 = +1, mag max(0.75*2-0.25,0) = 1.25
     np.testing.assert_allclose(post[0], [2.125, -3.125, 1.75], rtol=1e-15)
+
+
+def test_minsum_message_clip():
+    # |r| is clipped to 30, the sum-product rule's clip: with unit weights a
+    # degree-3 check over (50, 60, -70) sends min(60, 30), min(50, 30), min(50, 30)
+    base = np.array([[1, 1, 1]], dtype=np.int8)
+    shifts = np.zeros((1, 3), np.int32)
+    llr = np.array([[50.0, 60.0, -70.0]], dtype=np.float32)
+    s = np.array([[0]], dtype=np.uint8)
+    ws = np.ones((1, 1, 2))
+    wo = np.zeros((1, 1, 2))
+    _, post, _ = oracle.decode(base, shifts, 1, llr, s, 1, rule=oracle.RULE_MINSUM,
+                               w_scale=ws, w_offset=wo)
+    # edge 0: others (60, -70) -> -30; edge 1: others (50, -70) -> -30; edge 2: (50, 60) -> +30
+    np.testing.assert_array_equal(post[0], [20.0, 30.0, -40.0])
+    # offset below the clip: 1.0 * 60 - 35 = 25 < 30 for edge 0
+    wo = np.full((1, 1, 2), 35.0)
+    _, post, _ = oracle.decode(base, shifts, 1, llr, s, 1, rule=oracle.RULE_MINSUM,
+                               w_scale=ws, w_offset=wo)
+    np.testing.assert_array_equal(post[0], [25.0, 45.0, -55.0])
 
 
 # --------------------------------------------------------------------------
@@ -424,6 +444,39 @@ def test_minsum_gradient_matches_central_differences():
             fd = (f(eps) - f(-eps)) / (2 * eps)
             an = (gs if which == "scale" else go)[idx]
             assert an == pytest.approx(fd, rel=1e-5, abs=1e-9), (which, idx)
+
+
+def test_minsum_gradient_with_the_message_clip_active():
+    # Core columns carry confident correct LLRs (magnitude 50) and degree-1
+    # columns confident wrong ones (45): checks send messages at the clip
+    # (|r| = 30) both ways, and the posteriors they reach stay wrong or small,
+    # so the loss depends on those messages while the clip holds them fixed.
+    code, fr, T, _, _ = _minsum_case(snr=0.3)
+    Z = code.Z
+    deg = np.repeat(code.base.sum(axis=0), Z)
+    sx = 1.0 - 2.0 * fr.x
+    llr = np.where(deg > 1, 50.0 * sx, -45.0 * sx).astype(np.float32)
+    rng = np.random.default_rng(3)
+    ws = 0.9 + 0.2 * rng.random((T, code.mb, 2))
+    wo = 0.1 * rng.random((T, code.mb, 2))
+    loss, gs, go = oracle.minsum_train(code.base, code.shifts, code.Z, llr, fr.syn, fr.x, T,
+                                       ws, wo)
+    eps = 1e-6
+    worst = 0.0
+    for idx in np.ndindex(ws.shape):
+        for which in ("scale", "offset"):
+            def f(delta):
+                a, b = ws.copy(), wo.copy()
+                (a if which == "scale" else b)[idx] += delta
+                return oracle.minsum_train(code.base, code.shifts, code.Z, llr, fr.syn, fr.x,
+                                           T, a, b)[0].sum()
+            fd = (f(eps) - f(-eps)) / (2 * eps)
+            an = (gs if which == "scale" else go)[idx]
+            worst = max(worst, abs(an - fd))
+            # the loss sum is O(100): central differences carry ~1e-8 of rounding;
+            # a gradient taken through a clipped message would be off by ~1e-2
+            assert an == pytest.approx(fd, rel=1e-5, abs=1e-6), (which, idx)
+    assert np.abs(gs).max() > 1e-3 and np.abs(go).max() > 1e-3   # the loss is not saturated
 
 
 def test_minsum_loss_is_the_mean_cross_entropy_of_the_decoder_posteriors():
