@@ -243,30 +243,47 @@ __device__ __forceinline__ float u_of(float q) {
     return ex2_ftz(-kLog2e * fminf(fabsf(q), kClipMax));
 }
 
-// Rows of degree D <= 4: one thread per check.  Each thread first gathers the
-// inputs of U checks (i, i + NT, ..., i + (U-1) NT) in straight-line code --
-// the source array of an edge is selected, not branched on, and checks past Z
-// load from a clamped (valid) index -- so that all U * (2D + 1) loads are in
-// flight together; then it computes and writes the U checks.  (Issuing the
-// next batch's loads before computing the current one measured slower at
-// every block size: at 1024 threads it spills, and fewer threads leave too
-// few warps to hide the arithmetic's own latency.)
+// Rows of degree D <= 4 use one thread per check.  Each thread first gathers
+// the inputs of U checks (i, i + NT, ..., i + (U-1) NT) in straight-line code
+// -- checks past Z load from a clamped (valid) index -- so that all of the
+// batch's loads are in flight together; then it computes and writes the U
+// checks.  (Issuing the next batch's loads before computing the current one
+// measured slower at every block size: at 1024 threads it spills, and fewer
+// threads leave too few warps to hide the arithmetic's own latency.)
 //   first: iteration 0 (old messages are zero and are not read)
-//   last : final iteration (degree-1 variables get their posterior)
+//   last : final or tested iteration (degree-1 variables get their posterior)
 #ifndef QCMET_BATCH_LOW
 #define QCMET_BATCH_LOW 2
 #endif
 template <int D>
 __host__ __device__ constexpr int batch_of() { return QCMET_BATCH_LOW; }
 
-template <int D, typename M>
-__device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_base,
-                                        const Frame<M> &fr, int Z, size_t stride, bool first,
-                                        bool last) {
+// Rows of degree DC + D1 <= 4 whose DC core edges come first and D1 degree-1
+// edges last (the layout's order).  As run_row, one thread per check and U
+// checks gathered together, but the edge kinds are known at compile time: the
+// core edges read the core posteriors and their message slot, the degree-1
+// edges the channel LLR, and the per-row column and slot bases are computed
+// once per row.
+template <int DC, int D1, typename M>
+__device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int check_base,
+                                              const Frame<M> &fr, int Z, size_t stride, bool first,
+                                              bool last) {
+    constexpr int D = DC + D1;
+    constexpr int NC = DC > 0 ? DC : 1;
     constexpr int U = batch_of<D>();
     const int step = blockDim.x;
+    const float *src[D];
+    int sh[D];
+    M *slot[NC];
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const int4 en = ent[e];
+        src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
+        sh[e] = en.y;
+        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+    }
     for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
-        float lv[U][D], ro[U][D];
+        float lv[U][D], ro[U][NC];
         unsigned par[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -274,15 +291,12 @@ __device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_
             par[k] = fr.syn[check_base + i] & 1u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                const int4 en = ent[e];
-                int j = i + en.y;
+                int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                // degree-1 variable: L_qn - L_rmn(old) is the channel LLR exactly
-                const float *src = en.z < 0 ? fr.ch : fr.post_core;
-                lv[k][e] = src[en.x + j];
-                const bool has_old = !first && en.z >= 0;
-                ro[k][e] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + i) : 0.0f;
+                lv[k][e] = src[e][j];
             }
+#pragma unroll
+            for (int e = 0; e < DC; ++e) ro[k][e] = first ? 0.0f : Msg<M>::load(slot[e] + i);
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -292,12 +306,25 @@ __device__ __forceinline__ void run_row(const int4 *__restrict__ ent, int check_
             unsigned p = par[k];
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                q[e] = lv[k][e] - ro[k][e];
+                q[e] = e < DC ? lv[k][e] - ro[k][e < DC ? e : 0] : lv[k][e];
                 p ^= q[e] < 0.0f ? 1u : 0u;
                 u[e] = u_of(q[e]);
             }
             exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
-                scatter_r<M>(ent[e], i, q[e], a, b, p, fr, Z, stride, last);
+                if (e >= DC && !last) return;
+                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
+                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                float rn = neg ? -mag : mag;
+                int j = i + sh[e];
+                j = j >= Z ? j - Z : j;
+                if (e < DC) {
+                    rn = Msg<M>::quantize(rn);
+                    Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
+                    const_cast<float *>(src[e])[j] = q[e] + rn;
+                } else {
+                    fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+                }
             });
         }
     }
@@ -356,15 +383,35 @@ template <typename M>
 __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int check_base,
                                              const Frame<M> &fr, int Z, size_t stride, bool first,
                                              bool last) {
+    if (degree <= 4) {
+        // core edges first: their count picks the specialisation
+        int dc = 0;
+        for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
+        switch (degree * 8 + dc) {
+#define QCMET_SPLIT_CASE(DD, CC) \
+    case DD * 8 + CC: run_row_split<CC, DD - CC, M>(ent, check_base, fr, Z, stride, first, last); break;
+            QCMET_SPLIT_CASE(1, 0)
+            QCMET_SPLIT_CASE(1, 1)
+            QCMET_SPLIT_CASE(2, 0)
+            QCMET_SPLIT_CASE(2, 1)
+            QCMET_SPLIT_CASE(2, 2)
+            QCMET_SPLIT_CASE(3, 0)
+            QCMET_SPLIT_CASE(3, 1)
+            QCMET_SPLIT_CASE(3, 2)
+            QCMET_SPLIT_CASE(3, 3)
+            QCMET_SPLIT_CASE(4, 0)
+            QCMET_SPLIT_CASE(4, 1)
+            QCMET_SPLIT_CASE(4, 2)
+            QCMET_SPLIT_CASE(4, 3)
+            QCMET_SPLIT_CASE(4, 4)
+#undef QCMET_SPLIT_CASE
+            default: break;
+        }
+        return;
+    }
     switch (degree) {
-#define QCMET_ROW_CASE(DD) \
-    case DD: run_row<DD, M>(ent, check_base, fr, Z, stride, first, last); break;
 #define QCMET_PAIR_CASE(DD) \
     case DD: run_row_pair<DD, M>(ent, check_base, fr, Z, stride, first, last); break;
-        QCMET_ROW_CASE(1)
-        QCMET_ROW_CASE(2)
-        QCMET_ROW_CASE(3)
-        QCMET_ROW_CASE(4)
         QCMET_PAIR_CASE(5)
         QCMET_PAIR_CASE(6)
         QCMET_PAIR_CASE(7)
@@ -377,7 +424,6 @@ __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int ch
         QCMET_PAIR_CASE(14)
         QCMET_PAIR_CASE(15)
         QCMET_PAIR_CASE(16)
-#undef QCMET_ROW_CASE
 #undef QCMET_PAIR_CASE
         default: break;
     }
@@ -417,15 +463,27 @@ __device__ __forceinline__ void scatter_minsum(const int4 &en, int i, float q, f
     }
 }
 
-// Rows of degree D <= 4, one thread per check (the gather of run_row).
-template <int D, typename M>
+// Rows of degree DC + D1 <= 4, core edges first (the gather of run_row_split).
+template <int DC, int D1, typename M>
 __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int check_base,
                                                const Frame<M> &fr, int Z, size_t stride, bool first,
                                                bool last, const float4 &wt) {
+    constexpr int D = DC + D1;
+    constexpr int NC = DC > 0 ? DC : 1;
     constexpr int U = QCMET_BATCH_MINSUM;
     const int step = blockDim.x;
+    const float *src[D];
+    int sh[D];
+    M *slot[NC];
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const int4 en = ent[e];
+        src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
+        sh[e] = en.y;
+        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+    }
     for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
-        float lv[U][D], ro[U][D];
+        float lv[U][D], ro[U][NC];
         unsigned par[U];
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -433,14 +491,12 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
             par[k] = fr.syn[check_base + i] & 1u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                const int4 en = ent[e];
-                int j = i + en.y;
+                int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                const float *src = en.z < 0 ? fr.ch : fr.post_core;
-                lv[k][e] = src[en.x + j];
-                const bool has_old = !first && en.z >= 0;
-                ro[k][e] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + i) : 0.0f;
+                lv[k][e] = src[e][j];
             }
+#pragma unroll
+            for (int e = 0; e < DC; ++e) ro[k][e] = first ? 0.0f : Msg<M>::load(slot[e] + i);
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -452,7 +508,7 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
             int i1 = -1;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                q[e] = lv[k][e] - ro[k][e];
+                q[e] = e < DC ? lv[k][e] - ro[k][e < DC ? e : 0] : lv[k][e];
                 p ^= q[e] < 0.0f ? 1u : 0u;
                 const float v = fabsf(q[e]);
                 if (v < m1) {
@@ -465,8 +521,21 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
             }
 #pragma unroll
             for (int e = 0; e < D; ++e) {
+                if (e >= DC && !last) continue;
                 const float mn = D == 1 ? kNoOtherEdge : (e == i1 ? m2 : m1);
-                scatter_minsum<M>(ent[e], i, q[e], mn, p, wt, fr, Z, stride, last);
+                const float a_e = (e >= DC ? wt.y : wt.x) * mn - (e >= DC ? wt.w : wt.z);
+                const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
+                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                float rn = neg ? -mag : mag;
+                int j = i + sh[e];
+                j = j >= Z ? j - Z : j;
+                if (e < DC) {
+                    rn = Msg<M>::quantize(rn);
+                    Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
+                    const_cast<float *>(src[e])[j] = q[e] + rn;
+                } else {
+                    fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+                }
             }
         }
     }
@@ -529,15 +598,35 @@ template <typename M>
 __device__ __forceinline__ void dispatch_row_minsum(int degree, const int4 *ent, int check_base,
                                                     const Frame<M> &fr, int Z, size_t stride,
                                                     bool first, bool last, const float4 &wt) {
+    if (degree <= 4) {
+        int dc = 0;
+        for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
+        switch (degree * 8 + dc) {
+#define QCMET_SPLIT_CASE(DD, CC) \
+    case DD * 8 + CC:                                                                        \
+        run_row_minsum<CC, DD - CC, M>(ent, check_base, fr, Z, stride, first, last, wt); break;
+            QCMET_SPLIT_CASE(1, 0)
+            QCMET_SPLIT_CASE(1, 1)
+            QCMET_SPLIT_CASE(2, 0)
+            QCMET_SPLIT_CASE(2, 1)
+            QCMET_SPLIT_CASE(2, 2)
+            QCMET_SPLIT_CASE(3, 0)
+            QCMET_SPLIT_CASE(3, 1)
+            QCMET_SPLIT_CASE(3, 2)
+            QCMET_SPLIT_CASE(3, 3)
+            QCMET_SPLIT_CASE(4, 0)
+            QCMET_SPLIT_CASE(4, 1)
+            QCMET_SPLIT_CASE(4, 2)
+            QCMET_SPLIT_CASE(4, 3)
+            QCMET_SPLIT_CASE(4, 4)
+#undef QCMET_SPLIT_CASE
+            default: break;
+        }
+        return;
+    }
     switch (degree) {
-#define QCMET_ROW_CASE(DD) \
-    case DD: run_row_minsum<DD, M>(ent, check_base, fr, Z, stride, first, last, wt); break;
 #define QCMET_PAIR_CASE(DD) \
     case DD: run_row_pair_minsum<DD, M>(ent, check_base, fr, Z, stride, first, last, wt); break;
-        QCMET_ROW_CASE(1)
-        QCMET_ROW_CASE(2)
-        QCMET_ROW_CASE(3)
-        QCMET_ROW_CASE(4)
         QCMET_PAIR_CASE(5)
         QCMET_PAIR_CASE(6)
         QCMET_PAIR_CASE(7)
@@ -550,7 +639,6 @@ __device__ __forceinline__ void dispatch_row_minsum(int degree, const int4 *ent,
         QCMET_PAIR_CASE(14)
         QCMET_PAIR_CASE(15)
         QCMET_PAIR_CASE(16)
-#undef QCMET_ROW_CASE
 #undef QCMET_PAIR_CASE
         default: break;
     }

@@ -183,14 +183,17 @@ int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb
         dr.first_entry = (int32_t)ents.size();
         dr.check_base = r * Z;
         dr.row = r;
+        // core columns first, then degree-1 columns: the kernel specialises a
+        // row on (core edges, degree-1 edges)
         int32_t deg = 0;
-        for (int32_t k = 0; k < nb; ++k) {
-            const size_t i = (size_t)r * nb + k;
-            if (!c.base[i]) continue;
-            const int32_t vb = col_core[k] >= 0 ? col_core[k] * Z : k * Z;
-            ents.push_back(DevEntry{vb, c.shifts[i], slot[i], k});
-            ++deg;
-        }
+        for (int pass = 0; pass < 2; ++pass)
+            for (int32_t k = 0; k < nb; ++k) {
+                const size_t i = (size_t)r * nb + k;
+                if (!c.base[i] || (col_core[k] >= 0) != (pass == 0)) continue;
+                const int32_t vb = col_core[k] >= 0 ? col_core[k] * Z : k * Z;
+                ents.push_back(DevEntry{vb, c.shifts[i], slot[i], k});
+                ++deg;
+            }
         dr.degree = deg;
         w.push_back(dr.first_entry);
         w.push_back(dr.degree);
