@@ -67,3 +67,48 @@ def test_single_process_max_is_identity():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_mbit_per_s(1, 128, 10**6, 0.128) == pytest.approx(1000.0)
+
+
+def _decode_worker(rank, world, port, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    import oracle
+    import synth
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        code = synth.make_code("0.1", 8)
+        K = 3
+        fr = synth.make_frames(code, K, 0.3, first=bench.frame_offset(rank, K))
+        hard, post, ok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 4)
+        gathered = [None] * world
+        dist.all_gather_object(gathered, (hard.tolist(), ok.tolist()))
+        out[rank] = gathered
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_decode_equals_one_process_decoding_every_frame():
+    # frames are independent: the ranks' shards, concatenated in rank order,
+    # decode exactly as one process decoding all of them
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_decode_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import oracle
+    import synth
+    code = synth.make_code("0.1", 8)
+    fr = synth.make_frames(code, world * 3, 0.3)
+    hard, _, ok = oracle.decode(code.base, code.shifts, code.Z, fr.llr, fr.syn, 4)
+    for r in range(world):
+        got_hard = np.concatenate([np.array(res[r][k][0]) for k in range(world)])
+        got_ok = np.concatenate([np.array(res[r][k][1]) for k in range(world)])
+        np.testing.assert_array_equal(got_hard, hard)
+        np.testing.assert_array_equal(got_ok, ok)
