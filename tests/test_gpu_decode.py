@@ -320,6 +320,87 @@ def test_l2_persist_window_changes_no_result(q, full):
     np.testing.assert_array_equal(p3, p[:3].cpu().numpy())
 
 
+def test_maximum_size_frames(q):
+    # The largest frame the boundary accepts, n = 4 Z = 2^31 - 4 (Z = 2^29 - 1,
+    # odd, so rows end in a ragged pass), two frames so that frame offsets pass
+    # 2^31 elements, one core-and-degree-1 row and one all-core row.  After one
+    # layered iteration a posterior depends only on its depth-2 neighbourhood,
+    # so sampled posteriors are recomputed exactly with the oracle's check
+    # rule; the ok flags are checked against H c = s recomputed with torch.
+    Z = (1 << 29) - 1
+    base = np.array([[1, 1, 1, 1], [1, 0, 1, 1]], dtype=np.int8)
+    rng = np.random.default_rng(11)
+    shifts = (rng.integers(0, Z, size=base.shape) * base).astype(np.int32)
+    shifts[0, 2] = Z - 1                     # a shift that wraps at once
+    K, n, m = 2, 4 * Z, 2 * Z
+    qc = q.Code(base, shifts, Z)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(5)
+    llr = torch.randn((K, n), generator=gen, device="cuda")
+    syn = torch.randint(0, 2, (K, m), generator=gen, device="cuda", dtype=torch.uint8)
+    # frame 1: a codeword x with s = H x, received strongly, so that it decodes (ok = 1)
+    x = torch.randint(0, 2, (n,), generator=gen, device="cuda", dtype=torch.uint8)
+    xv = x.view(4, Z)
+    for l in range(2):
+        acc = torch.zeros(Z, dtype=torch.uint8, device="cuda")
+        for c in range(4):
+            if base[l, c]:
+                acc ^= torch.roll(xv[c], -int(shifts[l, c]))
+        syn[1, l * Z:(l + 1) * Z] = acc
+    llr[1] = 4.0 * (1.0 - 2.0 * x.float()) + 0.5 * llr[1]
+    del x, xv, acc
+    hard, post, ok = q.decode(qc, llr, syn, 1)
+    torch.cuda.synchronize()
+    assert int(ok[1]) == 1
+
+    # H c = s per frame, from the GPU's hard decisions (torch ops, not the decoder)
+    for f in range(K):
+        hv = hard[f].view(4, Z)
+        good = True
+        for l in range(2):
+            acc = syn[f, l * Z:(l + 1) * Z].clone()
+            for c in range(4):
+                if base[l, c]:
+                    acc ^= torch.roll(hv[c], -int(shifts[l, c]))
+            good = good and not bool(acc.any())
+        assert int(ok[f]) == int(good)
+        del hv
+
+    def ch(f, c, j):
+        return float(llr[f, c * Z + j])
+
+    def row_msgs(f, l, i, L):
+        # messages of check (l, i) given the posteriors L(c, j) of its variables
+        cols = [c for c in range(4) if base[l, c]]
+        js = [(i + int(shifts[l, c])) % Z for c in cols]
+        qv = np.array([L(c, j) for c, j in zip(cols, js)])
+        r = oracle.check_update(qv, int(syn[f, l * Z + i]) & 1)
+        return dict(zip(zip(cols, js), qv + r))
+
+    def after_row0(f, c, j):
+        if not base[0, c]:
+            return ch(f, c, j)
+        i0 = (j - int(shifts[0, c])) % Z
+        return row_msgs(f, 0, i0, lambda cc, jj: ch(f, cc, jj))[(c, j)]
+
+    def after_row1(f, c, j):
+        if not base[1, c]:
+            return after_row0(f, c, j)
+        i1 = (j - int(shifts[1, c])) % Z
+        return row_msgs(f, 1, i1, lambda cc, jj: after_row0(f, cc, jj))[(c, j)]
+
+    picks = [(c, j) for c in range(4) for j in (0, 1, Z - 2, Z - 1)]
+    picks += [(int(c), int(j)) for c, j in zip(rng.integers(0, 4, 48), rng.integers(0, Z, 48))]
+    for f in range(K):
+        for c, j in picks:
+            want = after_row1(f, c, j)
+            got = float(post[f, c * Z + j])
+            assert abs(got - want) <= 1e-4 * max(abs(want), 1.0), (f, c, j, got, want)
+            assert int(hard[f, c * Z + j]) == int(got < 0.0)
+    del llr, syn, hard, post, ok
+    torch.cuda.empty_cache()
+
+
 # --------------------------------------------------------------------------
 # Early termination (Discussion, Table tabearly)
 
