@@ -17,10 +17,6 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqcmet.so")
-# Diagnostic variant: every device access is bounds- and alignment-checked and
-# a violation is recorded and skipped instead of touching memory.
-BUILD_CHECKED = os.path.join(HERE, "_build_checked")
-LIB_CHECKED = os.path.join(HERE, "libqcmet_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["layout.cpp", "api.cpp", "batch.cpp", "decode.cu", "learned.cu"]
@@ -43,11 +39,10 @@ def _deps():
     return paths
 
 
-def up_to_date(checked: bool = False) -> bool:
-    lib = LIB_CHECKED if checked else LIB
-    if not os.path.exists(lib):
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
         return False
-    t = os.path.getmtime(lib)
+    t = os.path.getmtime(LIB)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
@@ -60,39 +55,34 @@ def _compile(src: str, extra, build_dir: str) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
-    """Compile and link the library (or its checked variant); returns its path.
+def build(force: bool = False, verbose_ptxas: bool = False) -> str:
+    """Compile and link the library; returns its path.
 
     Holds an exclusive lock on the build folder so that processes that start
     together (one per GPU) build once.
     """
-    lib = LIB_CHECKED if checked else LIB
-    bdir = BUILD_CHECKED if checked else BUILD
-    if not force and up_to_date(checked):
-        return lib
-    os.makedirs(bdir, exist_ok=True)
-    with open(os.path.join(bdir, ".lock"), "w") as lock:
+    if not force and up_to_date():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    with open(os.path.join(BUILD, ".lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
-        if not force and up_to_date(checked):
-            return lib
-        return _build_locked(verbose_ptxas, checked)
+        if not force and up_to_date():
+            return LIB
+        return _build_locked(verbose_ptxas)
 
 
-def _build_locked(verbose_ptxas: bool, checked: bool = False) -> str:
-    LIBP = LIB_CHECKED if checked else LIB
-    bdir = BUILD_CHECKED if checked else BUILD
+def _build_locked(verbose_ptxas: bool) -> str:
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
-    defs = ["-DQCMET_DEVICE_CHECKS"] if checked else []
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(
-            lambda s: _compile(s, defs + (extra if s.endswith(".cu") else []), bdir), SOURCES))
-    tmp = LIBP + f".tmp{os.getpid()}"
+            lambda s: _compile(s, extra if s.endswith(".cu") else [], BUILD), SOURCES))
+    tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIBP)
-    return LIBP
+    os.replace(tmp, LIB)
+    return LIB
 
 
 if __name__ == "__main__":
