@@ -507,7 +507,7 @@ int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint
     a.w_offset = w_offset;
     a.loss = loss;
     std::string err;
-    st = qcmet::launch_learned_forward(a, true, stream, err);
+    st = qcmet::launch_learned_forward(a, stream, err);
     if (st) return fail(st, err);
     c.learned_last = a;
     c.learned_ready = true;

@@ -111,9 +111,9 @@ struct FrameView {
     float *msg;
 };
 
-// One check of a row: forward.  Returns the loss contribution of the degree-1
-// variables (training) in *loss_part.
-template <int D, bool TRAIN>
+// One check of a row: training forward.  Adds the loss contribution of the
+// degree-1 variables to loss_part and records q for the backward pass.
+template <int D>
 __device__ __forceinline__ void ms_check_forward(const LearnedArgs &a, const LearnedView &v,
                                                  const FrameView &fv, const int4 *ent, int l,
                                                  int check_base, int i, int t, bool last,
@@ -143,7 +143,6 @@ __device__ __forceinline__ void ms_check_forward(const LearnedArgs &a, const Lea
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         const bool deg1 = en.z < 0;
-        if (deg1 && !last && !TRAIN) continue;
         float mn = e == i1 ? m2 : m1;
         if (D == 1) mn = kNoOther;
         const float a_e = (deg1 ? ws1 : ws0) * mn - (deg1 ? wo1 : wo0);
@@ -154,19 +153,16 @@ __device__ __forceinline__ void ms_check_forward(const LearnedArgs &a, const Lea
         if (!deg1) {
             fv.msg[(size_t)en.z * stride + i] = r;
             fv.post[vv[e]] = L;
-            if (TRAIN) qhist_t[(size_t)en.z * stride + i] = q[e];
+            qhist_t[(size_t)en.z * stride + i] = q[e];
         } else {
             if (last) fv.post[vv[e]] = L;
-            if (TRAIN) {
-                const float sx = fv.x[vv[e]] ? -1.0f : 1.0f;
-                loss_part += softplusf(-sx * L);
-            }
+            const float sx = fv.x[vv[e]] ? -1.0f : 1.0f;
+            loss_part += softplusf(-sx * L);
         }
     }
     (void)l;
 }
 
-template <bool TRAIN>
 __device__ void ms_row_forward(const LearnedArgs &a, const LearnedView &v, const FrameView &fv,
                                int j, int t, bool last, float *qhist_t, float &loss_part) {
     const int4 row = v.rows[j];
@@ -179,8 +175,8 @@ __device__ void ms_row_forward(const LearnedArgs &a, const LearnedView &v, const
         switch (row.y) {
 #define QCMET_MS_CASE(DD)                                                                       \
     case DD:                                                                                    \
-        ms_check_forward<DD, TRAIN>(a, v, fv, ent, l, row.z, i, t, last, qhist_t, ws0, ws1, wo0, \
-                                    wo1, loss_part);                                            \
+        ms_check_forward<DD>(a, v, fv, ent, l, row.z, i, t, last, qhist_t, ws0, ws1, wo0, wo1,  \
+                             loss_part);                                                        \
         break;
             QCMET_MS_CASE(1)
             QCMET_MS_CASE(2)
@@ -204,10 +200,9 @@ __device__ void ms_row_forward(const LearnedArgs &a, const LearnedView &v, const
     }
 }
 
-// Forward: inference (TRAIN = false: hard decisions, posteriors, ok) or
-// training (TRAIN = true: loss per frame, q and core posteriors of every
-// iteration for the backward pass).
-template <bool TRAIN>
+// Training forward: loss per frame, and q and the core posteriors of every
+// iteration for the backward pass.  (Decoding with learned weights runs in the
+// fused decode kernel of decode.cu.)
 __global__ void __launch_bounds__(kThreads, 1) ms_forward_kernel(const LearnedArgs a) {
     extern __shared__ int4 smem_i4[];
     int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
@@ -220,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_forward_kernel(const LearnedAr
         FrameView fv;
         fv.ch = a.ch + (size_t)f * n;
         fv.syn = a.syn + (size_t)f * a.m;
-        fv.x = TRAIN ? a.x + (size_t)f * n : nullptr;
+        fv.x = a.x + (size_t)f * n;
         fv.post = a.post + (size_t)f * n;
         fv.msg = a.msgs + (size_t)f * a.msg_slots * stride;
         for (int c = 0; c < v.nb; ++c) {
@@ -232,13 +227,13 @@ __global__ void __launch_bounds__(kThreads, 1) ms_forward_kernel(const LearnedAr
         float loss_part = 0.0f;
         for (int t = 0; t < a.T; ++t) {
             const bool last = t == a.T - 1;
-            float *qh = TRAIN ? a.qhist + ((size_t)f * a.T + t) * a.msg_slots * stride : nullptr;
+            float *qh = a.qhist + ((size_t)f * a.T + t) * a.msg_slots * stride;
             for (int layer = 0; layer < v.n_layers; ++layer) {
                 for (int j = v.layer_first[layer]; j < v.layer_first[layer + 1]; ++j)
-                    ms_row_forward<TRAIN>(a, v, fv, j, t, last, qh, loss_part);
+                    ms_row_forward(a, v, fv, j, t, last, qh, loss_part);
                 __syncthreads();
             }
-            if (TRAIN) {
+            {
                 // loss of the core posteriors after iteration t, and their snapshot
                 float *Lh = a.Lhist + ((size_t)f * a.T + t) * core_vars;
                 for (int c = 0; c < v.nb; ++c) {
@@ -254,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) ms_forward_kernel(const LearnedAr
                 __syncthreads();
             }
         }
-        if (TRAIN) {
+        {
             // loss = sum / (T n); unconnected columns contribute their constant channel term
             for (int c = 0; c < v.nb; ++c) {
                 if (v.col_kind[c] != kColUnconnected) continue;
@@ -272,41 +267,6 @@ __global__ void __launch_bounds__(kThreads, 1) ms_forward_kernel(const LearnedAr
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
                 a.loss[f] = a.T > 0 ? s / ((float)a.T * (float)n) : 0.0f;
             }
-            __syncthreads();
-        } else {
-            // step 4: hard decisions and the syndrome test
-            for (int c = 0; c < v.nb; ++c) {
-                const int kind = v.col_kind[c];
-                const bool from_ch = kind == kColUnconnected || (kind == kColDegree1 && a.T == 0);
-                for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-                    const size_t idx = (size_t)c * Z + i;
-                    if (from_ch) fv.post[idx] = fv.ch[idx];
-                    a.hard[(size_t)f * n + idx] = fv.post[idx] < 0.0f ? 1 : 0;
-                }
-            }
-            __syncthreads();
-            const uint8_t *hard = a.hard + (size_t)f * n;
-            int fail = 0;
-            for (int j = 0; j < v.n_rows; ++j) {
-                const int4 row = v.rows[j];
-                for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-                    unsigned par = fv.syn[row.z + i] & 1u;
-                    for (int e = 0; e < row.y; ++e) {
-                        const int4 en = v.entries[row.x + e];
-                        int jj = i + en.y;
-                        jj = jj >= Z ? jj - Z : jj;
-                        par ^= hard[(size_t)en.w * Z + jj];
-                    }
-                    fail |= (int)par;
-                }
-            }
-            const int nz = sw[kHdrZeroRows];
-            const int32_t *zrows = sw + sw[kHdrOffZeroRows];
-            for (int zr = 0; zr < nz; ++zr)
-                for (int i = threadIdx.x; i < Z; i += blockDim.x)
-                    fail |= fv.syn[(size_t)zrows[zr] * Z + i] & 1;
-            fail = __syncthreads_or(fail);
-            if (threadIdx.x == 0) a.ok[f] = fail ? 0 : 1;
             __syncthreads();
         }
     }
@@ -512,10 +472,9 @@ int launch_learned(Kern kern, const LearnedArgs &a, size_t smem, void *stream, s
 
 }  // namespace
 
-int launch_learned_forward(const LearnedArgs &a, bool train, void *stream, std::string &err) {
+int launch_learned_forward(const LearnedArgs &a, void *stream, std::string &err) {
     const size_t smem = ((size_t)a.image_words + ((size_t)a.nb + 3) / 4 * 4) * sizeof(int32_t);
-    return train ? launch_learned(ms_forward_kernel<true>, a, smem, stream, err)
-                 : launch_learned(ms_forward_kernel<false>, a, smem, stream, err);
+    return launch_learned(ms_forward_kernel, a, smem, stream, err);
 }
 
 int launch_learned_backward(const LearnedArgs &a, void *stream, std::string &err) {

@@ -160,7 +160,7 @@ struct CheckRule {
     const float *w_offset = nullptr;
 };
 
-int launch_learned_forward(const LearnedArgs &a, bool train, void *stream, std::string &err);
+int launch_learned_forward(const LearnedArgs &a, void *stream, std::string &err);
 int launch_learned_backward(const LearnedArgs &a, void *stream, std::string &err);
 
 // One frame of a mixed batch (device array; decode.cu's batch kernel).
