@@ -332,50 +332,82 @@ __device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int 
 
 // Rows of degree 5..16: two lanes per check (lanes l and l ^ 16 of a warp).
 // Each lane owns E = ceil(D/2) edges; the lanes swap their partial products
-// and sign parities with one shuffle each.
+// and sign parities with one shuffle each.  As in the rows of degree <= 4, a
+// lane first issues the loads of all its edges (for UP rounds of checks) in
+// straight-line code -- source selected, not branched on; indices clamped to
+// a valid check and edge -- and then computes: gathering edge by edge waited
+// for each load in turn (the two degree-10 rows of the rate-0.1 code took a
+// third of the decode that way).
+#ifndef QCMET_BATCH_PAIR
+#define QCMET_BATCH_PAIR 1
+#endif
 template <int D, typename M>
 __device__ __forceinline__ void run_row_pair(const int4 *__restrict__ ent, int check_base,
                                              const Frame<M> &fr, int Z, size_t stride, bool first,
                                              bool last) {
     constexpr int E = (D + 1) / 2;
+    constexpr int UP = QCMET_BATCH_PAIR;
     const int lane = threadIdx.x & 31;
     const int part = lane >> 4;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    for (int i0 = warp * 16; i0 < Z; i0 += nwarps * 16) {
-        const int i = i0 + (lane & 15);
-        const bool valid = i < Z;
-        float q[E], u[E];
-        unsigned par = (valid && part == 0) ? (fr.syn[check_base + i] & 1u) : 0u;
+    for (int i0 = warp * 16 * UP; i0 < Z; i0 += nwarps * 16 * UP) {
+        // (more than five edges per lane: too many operands to hold, gather as used)
+        constexpr bool kBatch = E <= 5;
+        float lv[UP][E], ro[UP][E];
+        unsigned par[UP];
 #pragma unroll
-        for (int el = 0; el < E; ++el) {
-            const int e = part * E + el;
-            if (valid && e < D) {
-                q[el] = gather_q<M>(ent[e], i, fr, Z, stride, first);
-                par ^= q[el] < 0.0f ? 1u : 0u;
-                u[el] = u_of(q[el]);
-            } else {
-                q[el] = 0.0f;
-                u[el] = 0.0f;  // the identity factor I + 0 J
+        for (int k = 0; k < UP; ++k) {
+            const int ic = min(i0 + k * 16 + (lane & 15), Z - 1);
+            par[k] = part == 0 ? (fr.syn[check_base + ic] & 1u) : 0u;
+#pragma unroll
+            for (int el = 0; el < E && kBatch; ++el) {
+                const int e = min(part * E + el, D - 1);
+                const int4 en = ent[e];
+                int j = ic + en.y;
+                j = j >= Z ? j - Z : j;
+                const float *src = en.z < 0 ? fr.ch : fr.post_core;
+                lv[k][el] = src[en.x + j];
+                const bool has_old = !first && en.z >= 0;
+                ro[k][el] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + ic) : 0.0f;
             }
         }
-        // product over this lane's edges
-        float ta = 1.0f, tb = 0.0f;
 #pragma unroll
-        for (int el = 0; el < E; ++el) {
-            const float na = fmaf(u[el], tb, ta);
-            const float nb = fmaf(u[el], ta, tb);
-            ta = na;
-            tb = nb;
+        for (int k = 0; k < UP; ++k) {
+            const int i = i0 + k * 16 + (lane & 15);
+            const bool valid = i < Z;
+            float q[E], u[E];
+            unsigned p = par[k];
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const bool own = part * E + el < D;
+                if constexpr (kBatch) {
+                    q[el] = own ? lv[k][el] - ro[k][el] : 0.0f;
+                } else {
+                    q[el] = (own && valid) ? gather_q<M>(ent[part * E + el], i, fr, Z, stride, first)
+                                           : 0.0f;
+                }
+                p ^= (own && q[el] < 0.0f) ? 1u : 0u;
+                u[el] = own ? u_of(q[el]) : 0.0f;  // 0: the identity factor I + 0 J
+            }
+            // product over this lane's edges
+            float ta = 1.0f, tb = 0.0f;
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const float na = fmaf(u[el], tb, ta);
+                const float nb = fmaf(u[el], ta, tb);
+                ta = na;
+                tb = nb;
+            }
+            const float oa = __shfl_xor_sync(0xffffffffu, ta, 16);
+            const float ob = __shfl_xor_sync(0xffffffffu, tb, 16);
+            p ^= __shfl_xor_sync(0xffffffffu, p, 16);
+            if (!valid) continue;
+            exclusive_products<E>(u, oa, ob, [&](int el, float a, float b) {
+                const int e = part * E + el;
+                if (e < D) scatter_r<M>(ent[e], i, q[el], a, b, p, fr, Z, stride, last);
+            });
         }
-        const float oa = __shfl_xor_sync(0xffffffffu, ta, 16);
-        const float ob = __shfl_xor_sync(0xffffffffu, tb, 16);
-        par ^= __shfl_xor_sync(0xffffffffu, par, 16);
-        if (!valid) continue;
-        exclusive_products<E>(u, oa, ob, [&](int el, float a, float b) {
-            const int e = part * E + el;
-            if (e < D) scatter_r<M>(ent[e], i, q[el], a, b, par, fr, Z, stride, last);
-        });
     }
 }
 
@@ -556,8 +588,22 @@ __device__ __forceinline__ void run_row_pair_minsum(const int4 *__restrict__ ent
     for (int i0 = warp * 16; i0 < Z; i0 += nwarps * 16) {
         const int i = i0 + (lane & 15);
         const bool valid = i < Z;
+        const int ic = min(i, Z - 1);
         float q[E];
-        unsigned par = (valid && part == 0) ? (fr.syn[check_base + i] & 1u) : 0u;
+        unsigned par = part == 0 ? (fr.syn[check_base + ic] & 1u) : 0u;
+        // all of this lane's loads first (source selected; indices clamped), for
+        // at most five edges per lane; more are gathered as used
+        constexpr bool kBatch = E <= 5;
+        float lv[E], ro[E];
+#pragma unroll
+        for (int el = 0; el < E && kBatch; ++el) {
+            const int4 en = ent[min(part * E + el, D - 1)];
+            int j = ic + en.y;
+            j = j >= Z ? j - Z : j;
+            const float *src = en.z < 0 ? fr.ch : fr.post_core;
+            lv[el] = src[en.x + j];
+            ro[el] = (!first && en.z >= 0) ? Msg<M>::load(fr.msg + (size_t)en.z * stride + ic) : 0.0f;
+        }
         float m1 = INFINITY, m2 = INFINITY;
         int i1 = -1;
 #pragma unroll
@@ -565,7 +611,11 @@ __device__ __forceinline__ void run_row_pair_minsum(const int4 *__restrict__ ent
             const int e = part * E + el;
             q[el] = 0.0f;
             if (valid && e < D) {
-                q[el] = gather_q<M>(ent[e], i, fr, Z, stride, first);
+                if constexpr (kBatch) {
+                    q[el] = lv[el] - ro[el];
+                } else {
+                    q[el] = gather_q<M>(ent[e], i, fr, Z, stride, first);
+                }
                 par ^= q[el] < 0.0f ? 1u : 0u;
                 const float v = fabsf(q[el]);
                 if (v < m1) {
