@@ -375,6 +375,8 @@ def run_report(args):
 
     import paper_2004_09084_gb300 as q
     dev = torch.device("cuda", 0)
+    # the decodes use the persisting L2 window as the bench line does (--l2-persist)
+    l2p = args.l2_persist == "on"
 
     def timed(fn, reps=3):
         fn()
@@ -396,10 +398,11 @@ def run_report(args):
             fr = synth.make_frames(code, K_FRAMES, snr, first=50_000)
             llr = torch.from_numpy(fr.llr).to(dev)
             syn = torch.from_numpy(fr.syn).to(dev)
-            ms_fix, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T))
+            ms_fix, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T, l2_persist=l2p))
             fer_fix = float(np.mean(np.any(h.cpu().numpy() != fr.x, axis=1)))
             for every in (1, 5):
-                ms_et, (h2, _, ok2, it) = timed(lambda: q.decode_early_stop(qc, llr, syn, T, every))
+                ms_et, (h2, _, ok2, it) = timed(
+                    lambda: q.decode_early_stop(qc, llr, syn, T, every, l2_persist=l2p))
                 it = it.cpu().numpy()
                 print(json.dumps({
                     "report": "early-stop", "snr": snr, "max_iterations": T, "check_every": every,
@@ -423,7 +426,7 @@ def run_report(args):
             syn = torch.from_numpy(fr.syn).to(dev)
             _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, fr.llr[:1], fr.syn[:1], 5)
             for msg in ("fp32", "fp16", "bf16"):
-                ms, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T, msg=msg))
+                ms, (h, _, ok) = timed(lambda: q.decode(qc, llr, syn, T, msg=msg, l2_persist=l2p))
                 hn = h.cpu().numpy()
                 _, p5, _ = q.decode(qc, llr[:1], syn[:1], 5, msg=msg)
                 p5 = p5.cpu().numpy().astype(np.float64)[0]
@@ -478,6 +481,8 @@ def run_report(args):
                 gen.manual_seed(777)
                 llr, syn, x = learned.make_batch(qc, K_FRAMES, snr, snr, gen)
                 res = {}
+                # no L2 window here: qcmet_minsum_decode takes no options, so BP runs
+                # the same way for a like-for-like time
                 for name, fn in (("bp", lambda: q.decode(qc, llr, syn, T)),
                                  ("minsum", lambda: learned.decode(qc, llr, syn, plain_s, plain_o)),
                                  ("learned", lambda: learned.decode(qc, llr, syn, ws, wo))):
@@ -515,7 +520,8 @@ def run_report(args):
             create_s = time.perf_counter() - t0
             ms, _ = timed(lambda: b.run())
             # the same frames as one launch per (rate, length) group
-            ms_sep, _ = timed(lambda: [q.decode(qc, llr, syn, T, msg=msg) for qc, llr, syn in groups])
+            ms_sep, _ = timed(lambda: [q.decode(qc, llr, syn, T, msg=msg, l2_persist=l2p)
+                                       for qc, llr, syn in groups])
             print(json.dumps({"report": "batch", "frames": len(frames), "bits": bits, "msg": msg,
                               "iterations": T, "ms": ms, "mbit_s": bits / ms / 1e3,
                               "separate_launches_ms": ms_sep,

@@ -245,7 +245,7 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
 
 
 def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: int = 1,
-                      msg: str = "fp32", threads: int = 0, stream=None):
+                      msg: str = "fp32", threads: int = 0, stream=None, l2_persist: bool = False):
     """Decode with early termination (``qcmet_decode_early_stop``).
 
     Returns ``(hard, llr_post, ok, iterations_used)`` as CUDA tensors; the call
@@ -268,7 +268,7 @@ def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: in
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    opts = _options(msg, threads)
+    opts = _options(msg, threads, l2_persist)
     _check(lib.qcmet_decode_early_stop(code.handle, llr.data_ptr(), syn.data_ptr(), K,
                                        int(max_iterations), int(check_every), hard.data_ptr(),
                                        post.data_ptr(), ok.data_ptr(), iters.data_ptr(),
