@@ -292,6 +292,22 @@ def test_full_size_fixed_iterations_properties(q, full):
     np.testing.assert_array_equal(ok2, ok)
 
 
+def test_host_entry_point_at_full_size(q, full):
+    # the host-buffer entry point at the bench size equals the device entry point
+    code, fr = full
+    qc = q.Code(code.base, code.shifts, code.Z)
+    h, p, ok = q.decode(qc, torch.from_numpy(fr.llr).cuda(), torch.from_numpy(fr.syn).cuda(), 3)
+    torch.cuda.synchronize()
+    h2, p2, ok2 = q.decode_host(qc, fr.llr, fr.syn, 3)
+    np.testing.assert_array_equal(h2, h.cpu().numpy())
+    np.testing.assert_array_equal(p2, p.cpu().numpy())
+    np.testing.assert_array_equal(ok2, ok.cpu().numpy())
+    h3, p3, ok3 = q.decode_host(qc, fr.llr, fr.syn, 3, want_post=False, l2_persist=True)
+    assert p3 is None
+    np.testing.assert_array_equal(h3, h2)
+    np.testing.assert_array_equal(ok3, ok2)
+
+
 def test_block_size_does_not_change_results_at_full_size(q, full):
     # one warp per frame against the default 1024 threads: per check the
     # arithmetic is the same, so the results are identical
