@@ -21,7 +21,13 @@
 //    warp's gathers are contiguous runs of 128 B (one wrap at most).
 //  * Degree-1 variables (a base column with a single circulant) keep no state:
 //    for them L_qn - L_rmn(old) equals the channel LLR exactly, so q is read
-//    from the channel array and L_qn is written once, in the last iteration.
+//    from the channel array and L_qn is written only in tested iterations
+//    (the last one, or each early-termination test).
+//  * Row paths: degree <= 4, one thread per check, specialised at compile
+//    time on the row's (core, degree-1) edge counts (the layout lists core
+//    edges first), with the loads of two checks issued together; degree
+//    5..16, two lanes per check, each lane's loads issued together for up to
+//    five edges per lane.  The same paths carry the learned min-sum rule.
 //  * No software prefetch: bulk L2 prefetches of the next row's operands
 //    were evicted before use often enough to add about a third to the DRAM
 //    reads, and the decode ran faster without them.

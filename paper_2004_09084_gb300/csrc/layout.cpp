@@ -6,7 +6,9 @@
 // index file of (shift, row, column) triples with column degrees (Results,
 // the H_compact1 paragraph), and the merging of unrelated base rows into one
 // layer (Results, Eqs. (m1), (m2)).  The table is our own format: per layer a
-// list of rows, per row a list of (column offset, shift, message slot).
+// list of rows, per row a list of (variable offset, shift, message slot,
+// column) with the row's core columns (degree > 1) first, so that the kernel
+// can specialise a row on its (core, degree-1) edge counts.
 #include <algorithm>
 #include <cstring>
 

@@ -63,6 +63,32 @@ def test_learned_decode_matches_the_oracle(q, learned, Z, K):
         np.testing.assert_array_equal(ok.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("seed,lo,hi", [(0, 1, 4), (1, 5, 10), (2, 11, 16)])
+def test_learned_decode_for_row_degrees_up_to_the_limit(q, learned, seed, lo, hi):
+    # every row path of the min-sum rule: one thread per check (degree <= 4),
+    # two lanes per check with the loads issued together (5..10) or gathered
+    # as used (11..16)
+    rng = np.random.default_rng(seed)
+    mb, nb, Z = 6, 18, 37
+    base = np.zeros((mb, nb), np.int8)
+    for l in range(mb):
+        base[l, rng.choice(nb, int(rng.integers(lo, hi + 1)), replace=False)] = 1
+    shifts = np.where(base == 1, rng.integers(0, Z, size=base.shape), 0).astype(np.int32)
+    code = synth.Code(base=base, shifts=shifts, Z=Z)
+    x = rng.integers(0, 2, size=(3, code.n), dtype=np.uint8)
+    llr = ((1.0 - 2.0 * x) * 2.0 + rng.normal(0, 2.0, size=x.shape)).astype(np.float32)
+    syn = synth.syndrome(code, x)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    T = 1
+    ws, wo = weights(code, T, seed=seed)
+    h, p, ok = learned.decode(qc, torch.from_numpy(llr).cuda(), torch.from_numpy(syn).cuda(),
+                              torch.from_numpy(ws).cuda(), torch.from_numpy(wo).cuda())
+    torch.cuda.synchronize()
+    _, rp, _ = oracle.decode(code.base, code.shifts, code.Z, llr, syn, T, rule=oracle.RULE_MINSUM,
+                             w_scale=ws.astype(np.float64), w_offset=wo.astype(np.float64))
+    assert rel_err(p.cpu().numpy(), rp).max() <= 1e-4
+
+
 def test_learned_decode_agrees_in_distribution_over_more_iterations(q, learned):
     # at an SNR where min-sum converges, both reach the same decisions
     code = synth.make_code("0.1", 64)
