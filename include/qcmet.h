@@ -119,8 +119,10 @@ int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *laye
  * the launch carries a persisting access-policy window over them.  The first
  * such call raises the calling context's persisting-L2 limit
  * (cudaLimitPersistingL2CacheSize) to the window size when it is lower; that
- * limit belongs to the CUDA context and ends with it.  On a device without
- * persisting L2 the option is ignored.  It changes no result, only speed.
+ * limit belongs to the CUDA context and ends with it.  The option is ignored
+ * on a device without persisting L2 and when that state is larger than the
+ * device's largest window (a partial window measured slower than none).  It
+ * changes no result, only speed.
  */
 typedef struct {
     int32_t msg_format;        /* QCMET_MSG_*; 0 = FP32                               */
