@@ -25,9 +25,13 @@
 //    (the last one, or each early-termination test).
 //  * Row paths: degree <= 4, one thread per check, specialised at compile
 //    time on the row's (core, degree-1) edge counts (the layout lists core
-//    edges first), with the loads of two checks issued together; degree
-//    5..16, two lanes per check, each lane's loads issued together for up to
-//    five edges per lane.  The same paths carry the learned min-sum rule.
+//    edges first).  With FP32 messages and the sum-product rule these rows
+//    are software-pipelined through shared memory: each thread copies the
+//    next check's operands with cp.async while it computes the current one.
+//    Other formats and the min-sum rule issue the loads of two checks
+//    together instead.  Degree 5..16: two lanes per check, each lane's loads
+//    issued together for up to five edges per lane.  The same paths carry
+//    the learned min-sum rule.
 //  * No software prefetch: bulk L2 prefetches of the next row's operands
 //    were evicted before use often enough to add about a third to the DRAM
 //    reads, and the decode ran faster without them.
@@ -47,6 +51,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <type_traits>
 #include <mutex>
 
 #include "qcmet_internal.h"
@@ -336,6 +341,134 @@ __device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int 
     }
 }
 
+// Dynamic shared memory of the decode kernels.  The FP32 sum-product kernel
+// keeps its staging area at offset 0 (so staging offsets are immediates) and
+// the schedule image after it; the other kernels hold only the image.
+extern __shared__ int4 qcmet_dyn_smem[];
+
+// ---- asynchronous copies, global -> shared (4 bytes, per thread) ----------
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Two rounds: one computed, one in flight.  Three and four measured no faster
+// (the rows are then limited by the SM's own issue and memory throughput).
+#ifndef QCMET_ASYNC_STAGES
+#define QCMET_ASYNC_STAGES 2
+#endif
+constexpr int kAsyncStages = QCMET_ASYNC_STAGES;  // rounds in flight + 1
+constexpr int kAsyncMaxOps = 8;  // operands per check: D posteriors/LLRs + DC old messages, D <= 4
+// staging floats per thread
+constexpr int kAsyncStageFloats = kAsyncStages * kAsyncMaxOps;
+
+// run_row_split with FP32 messages, software-pipelined through shared memory:
+// a thread handles one check per round, and while it computes round r the
+// operands of rounds r + 1 .. r + S - 1 are being copied into its own staging
+// slots by cp.async, so the loads' latency overlaps the arithmetic without
+// holding registers.  Each thread reads only the slots it filled, so a
+// per-thread wait_group orders them; no block barrier is needed.  Rounds of
+// one row touch disjoint variables and message slots (a circulant is a
+// permutation), so copying later rounds before round r's stores reads no
+// value that those stores change.  The syndrome bytes of later rounds wait in
+// registers.  Staging: [S rounds][D + DC operands][kDefaultThreads] floats.
+template <int DC, int D1>
+__device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent, int check_base,
+                                                    const Frame<float> &fr, int Z, size_t stride,
+                                                    bool first, bool last) {
+    constexpr int D = DC + D1;
+    constexpr int NC = DC > 0 ? DC : 1;
+    constexpr int S = kAsyncStages;
+    constexpr int NOP = D + DC;
+    constexpr int SS = kDefaultThreads;       // staging stride, fixed so offsets are immediates
+    constexpr uint32_t kOp = SS * 4;          // bytes between operands
+    constexpr uint32_t kRound = NOP * kOp;    // bytes between rounds
+    const int step = blockDim.x;
+    const int tid = threadIdx.x;
+    if (tid >= Z) return;
+    float *stage = reinterpret_cast<float *>(qcmet_dyn_smem);
+    const float *src[D];
+    int sh[D];
+    float *slot[NC];
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const int4 en = ent[e];
+        src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
+        sh[e] = en.y;
+        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+    }
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stage + tid);
+    // copy the operands of check i into round buffer b (or nothing past Z); one group per round
+    auto issue = [&](int i, int b) {
+        if (i < Z) {
+            const uint32_t sb = s0 + (uint32_t)b * kRound;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                int j = i + sh[e];
+                j = j >= Z ? j - Z : j;
+                cp_async4(sb + e * kOp, src[e] + j);
+            }
+            if (!first) {
+#pragma unroll
+                for (int e = 0; e < DC; ++e) cp_async4(sb + (D + e) * kOp, slot[e] + i);
+            }
+        }
+        cp_async_commit();
+    };
+    unsigned sy[S];
+#pragma unroll
+    for (int r = 0; r < S - 1; ++r) {
+        const int i = tid + r * step;
+        sy[r] = i < Z ? fr.syn[check_base + i] : 0u;
+        issue(i, r);
+    }
+    int buf = 0;
+    for (int i = tid; i < Z; i += step) {
+        {
+            const int nx = i + (S - 1) * step;
+            int nb = buf + (S - 1);
+            nb = nb >= S ? nb - S : nb;
+            sy[S - 1] = nx < Z ? fr.syn[check_base + nx] : 0u;
+            issue(nx, nb);
+        }
+        cp_async_wait<S - 1>();
+        const float *sv = stage + tid + buf * (kRound / 4);
+        float q[D], u[D];
+        unsigned p = sy[0] & 1u;
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            const float lv = sv[e * SS];
+            q[e] = (e < DC && !first) ? lv - sv[(D + (e < DC ? e : 0)) * SS] : lv;
+            p ^= q[e] < 0.0f ? 1u : 0u;
+            u[e] = u_of(q[e]);
+        }
+        exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+            if (e >= DC && !last) return;
+            float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
+            mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+            const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+            const float rn = neg ? -mag : mag;
+            int j = i + sh[e];
+            j = j >= Z ? j - Z : j;
+            if (e < DC) {
+                slot[e < DC ? e : 0][i] = rn;
+                const_cast<float *>(src[e])[j] = q[e] + rn;
+            } else {
+                fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+            }
+        });
+#pragma unroll
+        for (int r = 0; r < S - 1; ++r) sy[r] = sy[r + 1];
+        buf = buf + 1 == S ? 0 : buf + 1;
+    }
+}
+
 // Rows of degree 5..16: two lanes per check (lanes l and l ^ 16 of a warp).
 // Each lane owns E = ceil(D/2) edges; the lanes swap their partial products
 // and sign parities with one shuffle each.  As in the rows of degree <= 4, a
@@ -417,10 +550,39 @@ __device__ __forceinline__ void run_row_pair(const int4 *__restrict__ ent, int c
     }
 }
 
-template <typename M>
+template <typename M, bool A = false>
 __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int check_base,
                                              const Frame<M> &fr, int Z, size_t stride, bool first,
                                              bool last) {
+    if constexpr (A) {
+        if (degree <= 4) {
+            int dc = 0;
+            for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
+            switch (degree * 8 + dc) {
+#define QCMET_ASYNC_CASE(DD, CC)                                                               \
+    case DD * 8 + CC:                                                                          \
+        run_row_split_async<CC, DD - CC>(ent, check_base, fr, Z, stride, first, last);        \
+        break;
+                QCMET_ASYNC_CASE(1, 0)
+                QCMET_ASYNC_CASE(1, 1)
+                QCMET_ASYNC_CASE(2, 0)
+                QCMET_ASYNC_CASE(2, 1)
+                QCMET_ASYNC_CASE(2, 2)
+                QCMET_ASYNC_CASE(3, 0)
+                QCMET_ASYNC_CASE(3, 1)
+                QCMET_ASYNC_CASE(3, 2)
+                QCMET_ASYNC_CASE(3, 3)
+                QCMET_ASYNC_CASE(4, 0)
+                QCMET_ASYNC_CASE(4, 1)
+                QCMET_ASYNC_CASE(4, 2)
+                QCMET_ASYNC_CASE(4, 3)
+                QCMET_ASYNC_CASE(4, 4)
+#undef QCMET_ASYNC_CASE
+                default: break;
+            }
+            return;
+        }
+    }
     if (degree <= 4) {
         // core edges first: their count picks the specialisation
         int dc = 0;
@@ -818,7 +980,7 @@ __device__ __noinline__ int syndrome_fails(const Sched s, const Frame<M> fr) {
 // memory.  Called by every thread of the block.
 enum : int { kRuleSumProduct = 0, kRuleMinSum = 1 };
 
-template <typename M, int R>
+template <typename M, int R, bool A = false>
 __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArgs &a, int f,
                                                  const float *w_scale, const float *w_offset) {
     const int Z = s.Z;
@@ -856,7 +1018,8 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
             for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
                 const int4 row = s.rows[j];
                 if constexpr (R == kRuleSumProduct) {
-                    dispatch_row<M>(row.y, s.entries + row.x, row.z, fr, Z, stride, first, check);
+                    dispatch_row<M, A>(row.y, s.entries + row.x, row.z, fr, Z, stride, first,
+                                       check);
                 } else {
                     const size_t w = ((size_t)t * s.mb + (size_t)row.w) * 2;
                     const float4 wt = make_float4(__ldg(w_scale + w), __ldg(w_scale + w + 1),
@@ -892,7 +1055,8 @@ template <typename M, int R>
 __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const DecodeArgs a,
                                                                     const float *w_scale,
                                                                     const float *w_offset) {
-    extern __shared__ int4 smem_i4[];
+    constexpr bool A = std::is_same<M, float>::value && R == kRuleSumProduct;
+    int4 *smem_i4 = qcmet_dyn_smem + (A ? kAsyncStageFloats * kDefaultThreads / 4 : 0);
     int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
     {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
@@ -900,7 +1064,8 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
     }
     __syncthreads();
     const Sched s = make_sched(sw);
-    for (int f = blockIdx.x; f < a.K; f += gridDim.x) decode_one_frame<M, R>(s, a, f, w_scale, w_offset);
+    for (int f = blockIdx.x; f < a.K; f += gridDim.x)
+        decode_one_frame<M, R, A>(s, a, f, w_scale, w_offset);
 }
 
 // Mixed batch: frames of several codes in one launch.  Persistent CTAs take
@@ -909,7 +1074,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
 // layer table into shared memory when the code changes, and decode it.
 template <typename M>
 __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const BatchArgs b) {
-    extern __shared__ int4 smem_i4[];
+    int4 *smem_i4 = qcmet_dyn_smem;
     int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
     __shared__ int s_next;
     int cur_code = -1;
@@ -965,7 +1130,9 @@ template <typename M, int R = kRuleSumProduct>
 int launch_typed(const DecodeArgs &a, int threads, void *stream, std::string &err,
                  size_t window_bytes = 0, float hit_ratio = 0.0f,
                  const CheckRule &rule = CheckRule()) {
-    const size_t smem = (size_t)a.image_words * sizeof(int32_t);
+    constexpr bool A = std::is_same<M, float>::value && R == kRuleSumProduct;
+    const size_t smem = (size_t)a.image_words * sizeof(int32_t) +
+                        (A ? (size_t)kAsyncStageFloats * kDefaultThreads * sizeof(float) : 0);
     auto kern = decode_kernel<M, R>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
