@@ -1074,7 +1074,8 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_kernel(const Decode
 // layer table into shared memory when the code changes, and decode it.
 template <typename M>
 __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const BatchArgs b) {
-    int4 *smem_i4 = qcmet_dyn_smem;
+    constexpr bool A = std::is_same<M, float>::value;
+    int4 *smem_i4 = qcmet_dyn_smem + (A ? kAsyncStageFloats * kDefaultThreads / 4 : 0);
     int32_t *sw = reinterpret_cast<int32_t *>(smem_i4);
     __shared__ int s_next;
     int cur_code = -1;
@@ -1113,7 +1114,7 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const 
         a.slot_stride = fd.slot_stride;
         a.check_every = 0;
         a.iters_used = nullptr;
-        decode_one_frame<M, kRuleSumProduct>(s, a, 0, nullptr, nullptr);
+        decode_one_frame<M, kRuleSumProduct, A>(s, a, 0, nullptr, nullptr);
     }
 }
 
@@ -1178,6 +1179,7 @@ template <typename M>
 int launch_batch_typed(const BatchArgs &b, int threads, int grid, size_t smem, void *stream,
                        std::string &err) {
     auto kern = decode_batch_kernel<M>;
+    if (std::is_same<M, float>::value) smem += (size_t)kAsyncStageFloats * kDefaultThreads * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
