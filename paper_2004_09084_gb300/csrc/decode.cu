@@ -27,7 +27,8 @@
 //    time on the row's (core, degree-1) edge counts (the layout lists core
 //    edges first).  With FP32 messages and the sum-product rule these rows
 //    are software-pipelined through shared memory: each thread copies the
-//    next check's operands with cp.async while it computes the current one.
+//    next round's operands with cp.async while it computes the current one,
+//    two adjacent checks per thread (8-byte accesses) when Z is even.
 //    Other formats and the min-sum rule issue the loads of two checks
 //    together instead.  Degree 5..16: two lanes per check, each lane's loads
 //    issued together for up to five edges per lane.  The same paths carry
@@ -366,7 +367,7 @@ __device__ __forceinline__ void cp_async_wait() {
 constexpr int kAsyncStages = QCMET_ASYNC_STAGES;  // rounds in flight + 1
 constexpr int kAsyncMaxOps = 8;  // operands per check: D posteriors/LLRs + DC old messages, D <= 4
 // staging floats per thread
-constexpr int kAsyncStageFloats = kAsyncStages * kAsyncMaxOps;
+constexpr int kAsyncStageFloats = kAsyncStages * kAsyncMaxOps * 2;  // room for the paired form
 
 // run_row_split with FP32 messages, software-pipelined through shared memory:
 // a thread handles one check per round, and while it computes round r the
@@ -469,6 +470,139 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
     }
 }
 
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+
+// run_row_split_async with two adjacent checks (i, i + 1), i even, per thread
+// and round, for even Z: the message slots of both checks form one aligned
+// 8-byte word, and so do a circulant's two variables when its shift is even
+// (then j is even and j + 1 < Z), for loads and stores alike; odd shifts take
+// two 4-byte accesses (j + 1 may wrap to 0), and the two syndrome bytes are
+// one 16-bit load.  On GB300 a thread's 4-byte accesses are limited per SM by
+// the number of requests rather than by bytes (about 48 GB/s per SM for
+// 4-byte copies against 81 for 8-byte ones), so fewer, wider requests move the
+// same bytes faster.  Staging: [2 rounds][D + DC operands][kDefaultThreads]
+// float2.  (Both checks' results are held until the paired stores; at 1024
+// threads that costs about 110 bytes of spills, which measured cheaper than
+// unpaired posterior stores.)
+template <int DC, int D1>
+__device__ __forceinline__ void run_row_split_async2(const int4 *__restrict__ ent, int check_base,
+                                                     const Frame<float> &fr, int Z, size_t stride,
+                                                     bool first, bool last) {
+    constexpr int D = DC + D1;
+    constexpr int NC = DC > 0 ? DC : 1;
+    constexpr int NOP = D + DC;
+    constexpr int SS = kDefaultThreads;
+    constexpr uint32_t kOp = SS * 8;        // bytes between operands
+    constexpr uint32_t kRound = NOP * kOp;  // bytes between rounds
+    const int step = 2 * (int)blockDim.x;
+    const int tid = threadIdx.x;
+    if (2 * tid >= Z) return;
+    float2 *stage = reinterpret_cast<float2 *>(qcmet_dyn_smem);
+    const float *src[D];
+    int sh[D];
+    float *slot[NC];
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const int4 en = ent[e];
+        src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
+        sh[e] = en.y;
+        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+    }
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stage + tid);
+    auto issue = [&](int i, int b) {
+        if (i < Z) {
+            const uint32_t sb = s0 + (uint32_t)b * kRound;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                int j = i + sh[e];
+                j = j >= Z ? j - Z : j;
+                if (sh[e] & 1) {
+                    const int j1 = j + 1 == Z ? 0 : j + 1;
+                    cp_async4(sb + e * kOp, src[e] + j);
+                    cp_async4(sb + e * kOp + 4, src[e] + j1);
+                } else {
+                    cp_async8(sb + e * kOp, src[e] + j);
+                }
+            }
+            if (!first) {
+#pragma unroll
+                for (int e = 0; e < DC; ++e) cp_async8(sb + (D + e) * kOp, slot[e] + i);
+            }
+        }
+        cp_async_commit();
+    };
+    unsigned sy = reinterpret_cast<const uint16_t *>(fr.syn + check_base)[tid];
+    issue(2 * tid, 0);
+    int buf = 0;
+    for (int i = 2 * tid; i < Z; i += step) {
+        const int nx = i + step;
+        const unsigned sy_next =
+            nx < Z ? reinterpret_cast<const uint16_t *>(fr.syn + check_base)[nx >> 1] : 0u;
+        issue(nx, buf ^ 1);
+        cp_async_wait<1>();
+        const float2 *sv = stage + tid + buf * (kRound / 8);
+        float2 rn2[NC], pc2[NC];
+        float pd[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            float q[D], u[D];
+            unsigned p = (sy >> (8 * c)) & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const float2 l2 = sv[e * SS];
+                const float lv = c ? l2.y : l2.x;
+                float ro = 0.0f;
+                if (e < DC && !first) {
+                    const float2 r2 = sv[(D + (e < DC ? e : 0)) * SS];
+                    ro = c ? r2.y : r2.x;
+                }
+                q[e] = e < DC ? lv - ro : lv;
+                p ^= q[e] < 0.0f ? 1u : 0u;
+                u[e] = u_of(q[e]);
+            }
+            exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+                if (e >= DC && !last) return;
+                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
+                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                const float rn = neg ? -mag : mag;
+                if (e < DC) {
+                    if (c) {
+                        rn2[e < DC ? e : 0].y = rn;
+                        pc2[e < DC ? e : 0].y = q[e] + rn;
+                    } else {
+                        rn2[e < DC ? e : 0].x = rn;
+                        pc2[e < DC ? e : 0].x = q[e] + rn;
+                    }
+                } else {
+                    pd[c] = q[e] + rn;
+                }
+            });
+        }
+        // stores: messages as aligned pairs, posteriors as pairs where the shift is even
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            if (e >= DC && !last) continue;
+            int j = i + sh[e];
+            j = j >= Z ? j - Z : j;
+            float *dst = e < DC ? const_cast<float *>(src[e]) : fr.post + (src[e] - fr.ch);
+            const float v0 = e < DC ? pc2[e < DC ? e : 0].x : pd[0];
+            const float v1 = e < DC ? pc2[e < DC ? e : 0].y : pd[1];
+            if (e < DC) *reinterpret_cast<float2 *>(slot[e < DC ? e : 0] + i) = rn2[e < DC ? e : 0];
+            if (sh[e] & 1) {
+                dst[j] = v0;
+                dst[j + 1 == Z ? 0 : j + 1] = v1;
+            } else {
+                *reinterpret_cast<float2 *>(dst + j) = make_float2(v0, v1);
+            }
+        }
+        sy = sy_next;
+        buf ^= 1;
+    }
+}
+
 // Rows of degree 5..16: two lanes per check (lanes l and l ^ 16 of a warp).
 // Each lane owns E = ceil(D/2) edges; the lanes swap their partial products
 // and sign parities with one shuffle each.  As in the rows of degree <= 4, a
@@ -561,7 +695,10 @@ __device__ __forceinline__ void dispatch_row(int degree, const int4 *ent, int ch
             switch (degree * 8 + dc) {
 #define QCMET_ASYNC_CASE(DD, CC)                                                               \
     case DD * 8 + CC:                                                                          \
-        run_row_split_async<CC, DD - CC>(ent, check_base, fr, Z, stride, first, last);        \
+        if ((Z & 1) == 0)                                                                      \
+            run_row_split_async2<CC, DD - CC>(ent, check_base, fr, Z, stride, first, last);   \
+        else                                                                                   \
+            run_row_split_async<CC, DD - CC>(ent, check_base, fr, Z, stride, first, last);    \
         break;
                 QCMET_ASYNC_CASE(1, 0)
                 QCMET_ASYNC_CASE(1, 1)
