@@ -147,8 +147,10 @@ typedef struct {
  * Every device pointer must be 16-byte aligned (ALIGNMENT otherwise) and
  * must not overlap another.  The library keeps per-handle device scratch for
  * the messages (K * msg_slots * Z values), grown on demand, and uploads the
- * code's layer table on the first call.  Errors: INVALID_ARG, ALIGNMENT, OOM,
- * CUDA, UNSUPPORTED.
+ * code's layer table on the first call.  Resources: one launch of min(K, SM
+ * count) thread blocks, each owning a frame at a time; with FP32 messages a
+ * block also takes 128 KiB of dynamic shared memory (operand staging) besides
+ * the layer table.  Errors: INVALID_ARG, ALIGNMENT, OOM, CUDA, UNSUPPORTED.
  */
 int qcmet_decode(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
                  int32_t K, int32_t iterations, uint8_t *hard, float *llr_post, uint8_t *ok,
