@@ -58,10 +58,15 @@ def peaks():
 
 
 def kernel_hash() -> str:
+    """sha256 (first 16 hex digits) of the kernel sources with // comments and
+    blank lines removed, so that a comment edit keeps a profile valid."""
     h = hashlib.sha256()
     for name in ("decode.cu", "qcmet_internal.h"):
-        with open(os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", name)) as f:
+            for line in f:
+                code = line.split("//", 1)[0].rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 

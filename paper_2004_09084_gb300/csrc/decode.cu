@@ -11,7 +11,9 @@
 // GB300 design (ours, not the paper's):
 //  * Frames are independent, so one CTA owns one frame for the whole decode
 //    and a layer boundary costs one block barrier.  The whole decode -- init,
-//    T x layers, hard decision, syndrome test -- is a single launch.
+//    T x layers, hard decision, syndrome test -- is a single launch.  The
+//    FP32 sum-product kernel runs 896-thread blocks by default (built with
+//    that launch bound, for more registers per thread).
 //  * Frame-major state: the posteriors L_qn of the core columns (degree > 1)
 //    live in a compact array [K][core_cols][Z] (FP32), messages [K][slot][Z]
 //    in FP32 / FP16 / BF16.  The compact array is the state every row
@@ -35,7 +37,9 @@
 //    the learned min-sum rule.
 //  * No software prefetch: bulk L2 prefetches of the next row's operands
 //    were evicted before use often enough to add about a third to the DRAM
-//    reads, and the decode ran faster without them.
+//    reads, and per-thread prefetches of the next row's first round add
+//    requests to the per-SM path that limits the rows; the decode ran faster
+//    without either.
 //  * The check rule is evaluated in the tanh-product form
 //    |r_e| = 2 atanh(prod_{k != e} tanh(|q_k|/2)), which equals
 //    Phi(sum_{k != e} Phi(|q_k|)) (Methods, step 2).  With u_k = exp(-|q_k|),
