@@ -284,19 +284,21 @@ def run_ours(args):
     pin_llr = torch.from_numpy(fr.llr).pin_memory()
     pin_syn = torch.from_numpy(fr.syn).pin_memory()
     pin_hard = torch.empty((K_FRAMES, n), dtype=torch.uint8).pin_memory()
+    pin_post = torch.empty((K_FRAMES, n), dtype=torch.float32).pin_memory()
     pin_ok = torch.empty((K_FRAMES,), dtype=torch.uint8).pin_memory()
-    host_out = (pin_hard.numpy(), None, pin_ok.numpy())
-    q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
+    # all three outputs of the call cross back: hard decisions, posteriors, ok flags
+    host_out = (pin_hard.numpy(), pin_post.numpy(), pin_ok.numpy())
+    q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, msg=args.msg,
                   stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, want_post=False, msg=args.msg,
+        q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, msg=args.msg,
                       stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
-    h2d = K_FRAMES * n * 4 + K_FRAMES * code.m
-    d2h = K_FRAMES * n + K_FRAMES
+    h2d = pin_llr.numel() * pin_llr.element_size() + pin_syn.numel() * pin_syn.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in (pin_hard, pin_post, pin_ok))
 
     # the committed ncu figure is for this workload with FP32 messages
     traffic = profiled_traffic() if args.msg == "fp32" else None
@@ -335,7 +337,8 @@ def run_ours(args):
                              f"{K_FRAMES * info['msg_slots'] * Z * mbytes / 1e9:.2f} GB per GPU)"},
             "fer": fer, "ok_rate": ok_rate,
             "e2e": {"value": job_mbit_per_s(world, K_FRAMES, n, e2e_s), "unit": "Mbit/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "outputs": "hard, llr_post, ok"},
             "gpu_launches": args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -223,9 +223,17 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
  * All calls share the one array and it keeps what the last call left; this
  * call rewrites everything it reads before reading it.  Calls whose work can
  * overlap on the GPU (different streams, or host threads) race on the array:
- * order them on one stream.  The first call on each device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture begins.
+ * order them on one stream.  Each call copies the code's layer table (a few
+ * KiB) from host memory into the array with cudaMemcpyAsync on `stream`.
+ *
+ * Set-up: the first call on each device (with that device current) looks up
+ * the array's device address with cudaGetSymbolAddress and keeps it for that
+ * device's CUDA context; make that first call before any stream capture
+ * begins.  A new context on the device (e.g. after cudaDeviceReset) is
+ * detected by its context id, and the next call looks the address up again.
+ * The array itself is placed in device memory when CUDA loads the library's
+ * device code on that device (by default, lazily, at the library's first
+ * kernel launch or symbol lookup there), not by this call.
  */
 int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint8_t *syndrome,
                          int32_t K, int32_t iterations, uint8_t *hard, float *llr_post,

@@ -53,6 +53,7 @@
 //    arguments to [Phi(30), 30].
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -1420,9 +1421,55 @@ constexpr size_t kNoAllocImageBytes = size_t(64) << 10;  // 64 KiB of it for the
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 std::mutex g_noalloc_mutex;
-void *g_noalloc_addr[64] = {nullptr};
+struct NoAllocSlot {
+    void *addr = nullptr;             // device address of g_noalloc_scratch
+    unsigned long long ctx_id = 0;    // the context it belongs to (cuCtxGetId, never 0)
+};
+NoAllocSlot g_noalloc_slot[64];
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+// Unique id (for the life of the process) of the calling thread's current CUDA
+// context, 0 when none is current.  The driver calls are reached through the
+// runtime's entry-point query, so the library needs no link to libcuda.  The
+// address of g_noalloc_scratch belongs to a context: after cudaDeviceReset the
+// device's new primary context has a new id and the address is looked up again.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+int current_context_id(unsigned long long *id, std::string &err) {
+    static std::once_flag once;
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess && r == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PfnCtxGetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &r) ==
+                cudaSuccess && r == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PfnCtxGetId>(f);
+    });
+    *id = 0;
+    if (!get_current || !get_id) {
+        err = "the CUDA driver does not provide cuCtxGetCurrent / cuCtxGetId";
+        return QCMET_ERR_CUDA;
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) {
+        err = "cuCtxGetCurrent failed";
+        return QCMET_ERR_CUDA;
+    }
+    if (!ctx) return QCMET_OK;
+    if (get_id(ctx, id) != CUDA_SUCCESS) {
+        err = "cuCtxGetId failed";
+        return QCMET_ERR_CUDA;
+    }
+    return QCMET_OK;
+}
+
+// Device address of g_noalloc_scratch in the current context: looked up once
+// per device and context, then cached.
 int noalloc_address(void **out, std::string &err) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1434,17 +1481,25 @@ int noalloc_address(void **out, std::string &err) {
         err = "device index above 63";
         return QCMET_ERR_UNSUPPORTED;
     }
+    unsigned long long id = 0;
+    int st = current_context_id(&id, err);
+    if (st) return st;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
+    NoAllocSlot &slot = g_noalloc_slot[dev];
+    if (!slot.addr || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
+        // also makes the runtime's context current when none was
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             err = std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e);
             return QCMET_ERR_CUDA;
         }
-        g_noalloc_addr[dev] = p;
+        st = current_context_id(&id, err);
+        if (st) return st;
+        slot.addr = p;
+        slot.ctx_id = id;
     }
-    *out = g_noalloc_addr[dev];
+    *out = slot.addr;
     return QCMET_OK;
 }
 
