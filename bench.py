@@ -247,7 +247,8 @@ def run_ours(args):
 
     def step():
         q.decode(qc, llr, syn, ITERS, hard=hard, llr_post=post, ok=ok, msg=args.msg,
-                 stream=stream, l2_persist=args.l2_persist == "on")
+                 stream=stream, l2_persist=args.l2_persist == "on", kernel=args.kernel,
+                 cluster=args.cluster)
 
     progress("inputs resident; warm-up")
     for _ in range(args.warmup):
@@ -289,13 +290,15 @@ def run_ours(args):
     # all three outputs of the call cross back: hard decisions, posteriors, ok flags
     host_out = (pin_hard.numpy(), pin_post.numpy(), pin_ok.numpy())
     q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, msg=args.msg,
-                  stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
+                  stream=stream, out=host_out, l2_persist=args.l2_persist == "on",
+                  kernel=args.kernel, cluster=args.cluster)
     e2e_steps = max(1, min(args.steps, 3))
     barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         q.decode_host(qc, pin_llr.numpy(), pin_syn.numpy(), ITERS, msg=args.msg,
-                      stream=stream, out=host_out, l2_persist=args.l2_persist == "on")
+                      stream=stream, out=host_out, l2_persist=args.l2_persist == "on",
+                      kernel=args.kernel, cluster=args.cluster)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     h2d = pin_llr.numel() * pin_llr.element_size() + pin_syn.numel() * pin_syn.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (pin_hard, pin_post, pin_ok))
@@ -375,7 +378,8 @@ def run_profile(args):
     progress("profile case: inputs resident")
     for k in range(args.launches):
         hard, post, ok = q.decode(qc, llr, syn, args.iters, msg=args.msg,
-                                  l2_persist=args.l2_persist == "on")
+                                  l2_persist=args.l2_persist == "on", kernel=args.kernel,
+                                  cluster=args.cluster)
         torch.cuda.synchronize(dev)
         progress(f"profile case: launch {k} done")
     print(json.dumps({"profile_case": {"frames": args.frames, "iters": args.iters,
@@ -557,6 +561,10 @@ def main():
     ap.add_argument("--msg", choices=["fp32", "fp16", "bf16"], default="fp32")
     ap.add_argument("--l2-persist", choices=["on", "off"], default="on",
                     help="persisting L2 window over the core posteriors")
+    ap.add_argument("--kernel", choices=["auto", "frame", "group"], default="auto",
+                    help="decode kernel (QCMET_KERNEL_*)")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="grouped kernel: cluster size (0 = chosen by the library)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true",
                     help="only run --launches decodes of --frames x --iters (for ncu captures)")

@@ -124,15 +124,38 @@ int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *laye
  * device's largest window (a partial window measured slower than none).  It
  * changes no result, only speed.
  */
+/*
+ * Decode kernels.  Both evaluate the same arithmetic per check and frame, so
+ * the choice changes no result, only speed and scratch:
+ *  QCMET_KERNEL_FRAME -- one thread block owns one frame for the whole decode
+ *     (frame-major state); the grid is min(K, SM count) blocks.  Serves every
+ *     call, including early termination and the min-sum rule.
+ *  QCMET_KERNEL_GROUP -- frames are taken four at a time and stored
+ *     interleaved (the four frames' values of a variable, a message or a
+ *     syndrome bit form one 16-byte word), and a thread-block cluster of
+ *     cluster_size blocks (0 = chosen by the library from the device's
+ *     cluster occupancy; else 1, 2, 4 or 8) shares the checks of each row of
+ *     one group, with one cluster barrier per layer.  Sum-product rule, fixed
+ *     iterations.  Scratch: ceil(K/4) * (16 n + 4 m + 16 core_columns Z +
+ *     msg_slots Z (16 for FP32, 8 for 16-bit messages)) bytes.
+ *  QCMET_KERNEL_AUTO (0) -- the library's choice.
+ */
+#define QCMET_KERNEL_AUTO 0
+#define QCMET_KERNEL_FRAME 1
+#define QCMET_KERNEL_GROUP 2
+
 typedef struct {
     int32_t msg_format;        /* QCMET_MSG_*; 0 = FP32                               */
-    int32_t threads_per_block; /* 0 = library default; else a multiple of 32, <= 1024 */
+    int32_t threads_per_block; /* frame kernel: 0 = library default; else a multiple
+                                  of 32, <= 1024 (the grouped kernel sizes its own)  */
     int32_t l2_persist;        /* 0 = off, 1 = persisting L2 window over the state  */
-    int32_t reserved[5];       /* set to 0                                          */
+    int32_t kernel;            /* QCMET_KERNEL_*                                    */
+    int32_t cluster_size;      /* grouped kernel: 0 = automatic, else 1, 2, 4 or 8  */
+    int32_t reserved[3];       /* set to 0                                          */
 } qcmet_decode_options;
-/* The default block is 896 threads for FP32 messages (a kernel built for that
- * size, with more registers per thread) and 1024 for FP16/BF16.  The block
- * size changes no result. */
+/* The frame kernel's default block is 896 threads for FP32 messages (a kernel
+ * built for that size, with more registers per thread) and 1024 for
+ * FP16/BF16.  The block size changes no result. */
 
 /*
  * Decode K frames with a fixed number of layered iterations (Methods, steps

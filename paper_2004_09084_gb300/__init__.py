@@ -38,6 +38,7 @@ MAX_ROW_DEGREE = 16
 
 MERGE = {"none": 0, "exact": 1, "greedy": 2}
 MSG = {"fp32": 0, "fp16": 1, "bf16": 2}
+KERNEL = {"auto": 0, "frame": 1, "group": 2}
 
 # every symbol the header declares
 EXPORTS = (
@@ -78,7 +79,8 @@ class BatchConfig(ctypes.Structure):
 
 class DecodeOptions(ctypes.Structure):
     _fields_ = [("msg_format", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("l2_persist", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("l2_persist", ctypes.c_int32), ("kernel", ctypes.c_int32),
+                ("cluster_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 def _load():
@@ -193,19 +195,24 @@ class Code:
             pass
 
 
-def _options(msg: str, threads: int, l2_persist: bool = False) -> DecodeOptions:
+def _options(msg: str, threads: int, l2_persist: bool = False, kernel: str = "auto",
+             cluster: int = 0) -> DecodeOptions:
     if msg not in MSG:
         raise ValueError(f"msg must be one of {sorted(MSG)}")
+    if kernel not in KERNEL:
+        raise ValueError(f"kernel must be one of {sorted(KERNEL)}")
     o = DecodeOptions()
     o.msg_format = MSG[msg]
     o.threads_per_block = int(threads)
     o.l2_persist = 1 if l2_persist else 0
+    o.kernel = KERNEL[kernel]
+    o.cluster_size = int(cluster)
     return o
 
 
 def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=None,
            msg: str = "fp32", threads: int = 0, stream=None, want_post: bool = True,
-           l2_persist: bool = False):
+           l2_persist: bool = False, kernel: str = "auto", cluster: int = 0):
     """Decode K frames on the GPU (``qcmet_decode_ex``).
 
     ``llr``: float32 CUDA tensor [K, n]; ``syn``: uint8 CUDA tensor [K, m].
@@ -213,6 +220,8 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     (``llr_post`` is None when ``want_post`` is false and none was passed).
     The call is asynchronous on ``stream`` (default: torch's current stream).
     ``l2_persist`` keeps the core posteriors in a persisting L2 window.
+    ``kernel`` is "auto", "frame" or "group" (``QCMET_KERNEL_*``); ``cluster``
+    the grouped kernel's cluster size (0 = automatic).
     """
     import torch
 
@@ -237,7 +246,7 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    opts = _options(msg, threads, l2_persist)
+    opts = _options(msg, threads, l2_persist, kernel, cluster)
     _check(lib.qcmet_decode_ex(code.handle, llr.data_ptr(), syn.data_ptr(), K, int(iterations),
                                hard.data_ptr(), llr_post.data_ptr() if llr_post is not None else None,
                                ok.data_ptr(), ctypes.byref(opts), sptr))
@@ -245,7 +254,8 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
 
 
 def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: int = 1,
-                      msg: str = "fp32", threads: int = 0, stream=None, l2_persist: bool = False):
+                      msg: str = "fp32", threads: int = 0, stream=None, l2_persist: bool = False,
+                      kernel: str = "auto"):
     """Decode with early termination (``qcmet_decode_early_stop``).
 
     Returns ``(hard, llr_post, ok, iterations_used)`` as CUDA tensors; the call
@@ -268,7 +278,7 @@ def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: in
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    opts = _options(msg, threads, l2_persist)
+    opts = _options(msg, threads, l2_persist, kernel)
     _check(lib.qcmet_decode_early_stop(code.handle, llr.data_ptr(), syn.data_ptr(), K,
                                        int(max_iterations), int(check_every), hard.data_ptr(),
                                        post.data_ptr(), ok.data_ptr(), iters.data_ptr(),
@@ -278,7 +288,7 @@ def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: in
 
 def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
                 want_post: bool = True, msg: str = "fp32", threads: int = 0, stream=None,
-                out=None, l2_persist: bool = False):
+                out=None, l2_persist: bool = False, kernel: str = "auto", cluster: int = 0):
     """Decode frames held in host memory (``qcmet_decode_host``); synchronous.
 
     ``out`` may supply preallocated (hard, llr_post, ok) host arrays, e.g. pinned.
@@ -294,7 +304,7 @@ def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
     for a, dt in ((llr, np.float32), (syn, np.uint8), (hard, np.uint8), (ok, np.uint8)):
         if a.dtype != dt or not a.flags.c_contiguous:
             raise ValueError("host arrays must be C-contiguous with the documented dtypes")
-    opts = _options(msg, threads, l2_persist)
+    opts = _options(msg, threads, l2_persist, kernel, cluster)
     sptr = 0
     if stream is not None:
         sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqcmet.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["layout.cpp", "api.cpp", "batch.cpp", "decode.cu", "learned.cu"]
+SOURCES = ["layout.cpp", "api.cpp", "batch.cpp", "decode.cu", "decode_group.cu", "learned.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
           f"-I{INCLUDE}"]

@@ -27,6 +27,15 @@ int cuda_fail(const char *what, cudaError_t e) {
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// QCMET_KERNEL_AUTO: the grouped kernel for fixed-iteration sum-product
+// decodes of at least four frames.
+bool use_group_by_default(const qcmet::Code &c, int32_t K) {
+    (void)c;
+    return K >= 4 && false;
+}
+
 size_t msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 4 : 2; }
 
 // Upload the schedule image once, on the current device.
@@ -74,12 +83,24 @@ int grow(void **buf, size_t *have, size_t need, const char *what) {
     return QCMET_OK;
 }
 
+struct KernelChoice {
+    int32_t kernel = QCMET_KERNEL_AUTO;
+    int32_t cluster = 0;
+};
+
 int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
-                  bool *l2_persist = nullptr) {
+                  bool *l2_persist = nullptr, KernelChoice *kc = nullptr) {
     *fmt = QCMET_MSG_FP32;
     *threads = 0;
     if (l2_persist) *l2_persist = false;
+    if (kc) *kc = KernelChoice();
     if (!o) return QCMET_OK;
+    if (o->kernel != QCMET_KERNEL_AUTO && o->kernel != QCMET_KERNEL_FRAME &&
+        o->kernel != QCMET_KERNEL_GROUP)
+        return fail(QCMET_ERR_INVALID_ARG, "unknown kernel");
+    if (o->cluster_size != 0 && o->cluster_size != 1 && o->cluster_size != 2 &&
+        o->cluster_size != 4 && o->cluster_size != 8)
+        return fail(QCMET_ERR_INVALID_ARG, "cluster_size must be 0, 1, 2, 4 or 8");
     if (o->msg_format != QCMET_MSG_FP32 && o->msg_format != QCMET_MSG_FP16 &&
         o->msg_format != QCMET_MSG_BF16)
         return fail(QCMET_ERR_INVALID_ARG, "unknown msg_format");
@@ -93,6 +114,10 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
     *fmt = o->msg_format;
     *threads = o->threads_per_block;
     if (l2_persist) *l2_persist = o->l2_persist == 1;
+    if (kc) {
+        kc->kernel = o->kernel;
+        kc->cluster = o->cluster_size;
+    }
     return QCMET_OK;
 }
 
@@ -132,6 +157,55 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
     return QCMET_OK;
 }
 
+// The grouped kernel (decode_group.cu) for K frames: interleaved scratch of
+// ceil(K/4) groups, one cluster per group.
+int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
+                 int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok, int32_t fmt,
+                 int32_t cluster, bool l2p, void *stream) {
+    qcmet::GroupLaunch L;
+    std::string err;
+    int st = qcmet::choose_group_launch(fmt, K, c.Z, (int32_t)c.image.words.size(), cluster, &L,
+                                        err);
+    if (st) return fail(st, err);
+    const size_t G = (size_t)L.groups;
+    const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
+    const size_t b_ch = round256(G * n * 16);
+    const size_t b_syn = round256(G * m * 4);
+    const size_t b_core = round256(G * (size_t)c.core_cols * c.Z * 16);
+    const size_t b_msg = round256(G * (size_t)c.msg_slots * c.Z * qcmet::group_msg_bytes(fmt));
+    st = grow(&c.d_group, &c.group_bytes, b_ch + b_syn + b_core + b_msg + 256,
+              "cudaMalloc(grouped scratch)");
+    if (st) return st;
+    char *p = static_cast<char *>(c.d_group);
+    size_t window = 0;
+    float hit = 0.0f;
+    if (l2p) {
+        st = l2_window(G * (size_t)c.core_cols * c.Z * 16, &window, &hit);
+        if (st) return st;
+    }
+    qcmet::GroupArgs a;
+    a.ch = llr_ch;
+    a.syn = syndrome;
+    a.post = llr_post;
+    a.hard = hard;
+    a.ok = ok;
+    a.ch4 = p;
+    a.syn4 = reinterpret_cast<uint32_t *>(p + b_ch);
+    a.core4 = p + b_ch + b_syn;
+    a.msgs4 = p + b_ch + b_syn + b_core;
+    a.image = c.d_image;
+    a.image_words = (int32_t)c.image.words.size();
+    a.K = K;
+    a.T = T;
+    a.n = (int32_t)n;
+    a.m = (int32_t)m;
+    a.core_cols = c.core_cols;
+    a.msg_slots = c.msg_slots;
+    st = qcmet::launch_decode_group(a, fmt, L, stream, err, window, hit);
+    if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
 int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                   int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok,
                   const qcmet_decode_options *opts, void *stream, int32_t check_every = 0,
@@ -139,7 +213,8 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
                   const float *w_offset = nullptr) {
     int32_t fmt, threads;
     bool l2p = false;
-    int st = check_options(opts, &fmt, &threads, &l2p);
+    KernelChoice kc;
+    int st = check_options(opts, &fmt, &threads, &l2p, &kc);
     if (st) return st;
     if (K < 0) return fail(QCMET_ERR_INVALID_ARG, "K must be >= 0");
     if (T < 0) return fail(QCMET_ERR_INVALID_ARG, "iterations must be >= 0");
@@ -151,6 +226,14 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
         return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
     st = ensure_device(c);
     if (st) return st;
+    const bool group_ok = check_every == 0 && !w_scale;
+    if (kc.kernel == QCMET_KERNEL_GROUP && !group_ok)
+        return fail(QCMET_ERR_UNSUPPORTED,
+                    "the grouped kernel serves the sum-product rule with fixed iterations only");
+    if (kc.kernel == QCMET_KERNEL_GROUP || (kc.kernel == QCMET_KERNEL_AUTO && group_ok &&
+                                            use_group_by_default(c, K)))
+        return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc.cluster, l2p,
+                            stream);
 
     const size_t n = (size_t)c.nb * c.Z;
     const size_t stride = qcmet::slot_stride(c.Z);
@@ -209,8 +292,6 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     return QCMET_OK;
 }
 
-size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
 }  // namespace
 
 namespace qcmet {
@@ -255,6 +336,7 @@ void qcmet_code_destroy(qcmet_code *code) {
     if (c.d_post) cudaFree(c.d_post);
     if (c.d_core) cudaFree(c.d_core);
     if (c.d_io) cudaFree(c.d_io);
+    if (c.d_group) cudaFree(c.d_group);
     if (c.d_learned) cudaFree(c.d_learned);
     delete code;
 }

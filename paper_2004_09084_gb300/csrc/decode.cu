@@ -60,17 +60,12 @@
 #include <type_traits>
 #include <mutex>
 
+#include "check_rule.cuh"
 #include "qcmet_internal.h"
 
 namespace qcmet {
 
 namespace {
-
-constexpr float kClipMax = 30.0f;
-// Phi(30) = 2 atanh(exp(-30)), the lower end of the clipping interval.
-constexpr float kClipMin = 1.8715246e-13f;
-constexpr float kLn2 = 0.693147180559945309f;
-constexpr float kLog2e = 1.442695040888963407f;
 #ifndef QCMET_THREADS
 #define QCMET_THREADS 1024
 #endif
@@ -87,90 +82,6 @@ constexpr int kDefaultThreads = QCMET_THREADS;
 constexpr int kFp32Threads = QCMET_FP32_THREADS;
 static_assert(kFp32Threads % 32 == 0 && kFp32Threads <= kDefaultThreads, "FP32 block size");
 
-// ---- transcendentals --------------------------------------------------------
-//
-// The check rule takes exp2 of arguments in [-30 log2(e), 0] and log2 of
-// alpha >= 1 and beta >= exp(-30) (beta = 0 only for a check of degree 1,
-// whose log is -inf and whose magnitude clips to 30).  No argument or result
-// is subnormal, so the flush-to-zero forms of the hardware approximations
-// return what the non-flushing ones do, without the subnormal handling.
-__device__ __forceinline__ float ex2_ftz(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float lg2_ftz(float x) {
-    float y;
-    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// ---- message storage formats ---------------------------------------------
-
-template <typename M>
-struct Msg;
-
-template <>
-struct Msg<float> {
-    static __device__ __forceinline__ float load(const float *p) { return *p; }
-    static __device__ __forceinline__ float quantize(float x) { return x; }
-    static __device__ __forceinline__ void store(float *p, float x) { *p = x; }
-};
-
-template <>
-struct Msg<__half> {
-    static __device__ __forceinline__ float load(const __half *p) { return __half2float(*p); }
-    static __device__ __forceinline__ float quantize(float x) {
-        return __half2float(__float2half_rn(x));
-    }
-    static __device__ __forceinline__ void store(__half *p, float x) { *p = __float2half_rn(x); }
-};
-
-template <>
-struct Msg<__nv_bfloat16> {
-    static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
-        return __bfloat162float(*p);
-    }
-    static __device__ __forceinline__ float quantize(float x) {
-        return __bfloat162float(__float2bfloat16_rn(x));
-    }
-    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float x) {
-        *p = __float2bfloat16_rn(x);
-    }
-};
-
-// ---- shared-memory view of the schedule ------------------------------------
-
-struct Sched {
-    const int32_t *w;
-    int32_t n_rows, n_layers, nb, Z, mb, n_zero_rows;
-    const int32_t *layer_first;
-    const int4 *rows;     // DevRow
-    const int4 *entries;  // DevEntry
-    const int32_t *col_kind;
-    const int32_t *zero_rows;
-    const int32_t *col_core;  // [nb]: index among the core columns, or -1
-};
-
-__device__ __forceinline__ Sched make_sched(const int32_t *w) {
-    Sched s;
-    s.w = w;
-    s.n_rows = w[kHdrRows];
-    s.n_layers = w[kHdrLayers];
-    s.nb = w[kHdrNb];
-    s.Z = w[kHdrZ];
-    s.mb = w[kHdrMb];
-    s.n_zero_rows = w[kHdrZeroRows];
-    s.layer_first = w + w[kHdrOffLayerFirst];
-    s.rows = reinterpret_cast<const int4 *>(w + w[kHdrOffRows]);
-    s.entries = reinterpret_cast<const int4 *>(w + w[kHdrOffEntries]);
-    s.col_kind = w + w[kHdrOffColKind];
-    s.zero_rows = w + w[kHdrOffZeroRows];
-    s.col_core = w + w[kHdrOffColCore];
-    return s;
-}
-
 // Per-frame views of the global arrays.
 template <typename M>
 struct Frame {
@@ -180,57 +91,6 @@ struct Frame {
     float *post_core;    // [core_cols][Z] posteriors of the core columns
     M *msg;              // [slots][stride]
 };
-
-// ---- one check node ----------------------------------------------------------
-
-// (a, b) (x) (c, d): product of two elements a I + b J and c I + d J.
-__device__ __forceinline__ void cmul(float a, float b, float c, float d, float &x, float &y) {
-    x = fmaf(a, c, b * d);
-    y = fmaf(a, d, b * c);
-}
-
-// For local edges e = 0..E-1 with u[e] = exp(-|q_e|), call
-// emit(e, alpha_e, beta_e) where alpha_e I + beta_e J is
-// (oa I + ob J) * prod_{k != e} (I + u_k J).
-template <int E, typename Emit>
-__device__ __forceinline__ void exclusive_products(const float (&u)[E], float oa, float ob,
-                                                   Emit &&emit) {
-    if constexpr (E <= 6) {
-        float pa[E], pb[E];
-        pa[0] = oa;
-        pb[0] = ob;
-#pragma unroll
-        for (int e = 1; e < E; ++e) {
-            pa[e] = fmaf(u[e - 1], pb[e - 1], pa[e - 1]);
-            pb[e] = fmaf(u[e - 1], pa[e - 1], pb[e - 1]);
-        }
-        float sa = 1.0f, sb = 0.0f;
-#pragma unroll
-        for (int e = E - 1; e >= 0; --e) {
-            float a, b;
-            cmul(pa[e], pb[e], sa, sb, a, b);
-            const float nsa = fmaf(u[e], sb, sa);
-            const float nsb = fmaf(u[e], sa, sb);
-            sa = nsa;
-            sb = nsb;
-            emit(e, a, b);
-        }
-    } else {
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-            float a = oa, b = ob;
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if (k == e) continue;
-                const float na = fmaf(u[k], b, a);
-                const float nb = fmaf(u[k], a, b);
-                a = na;
-                b = nb;
-            }
-            emit(e, a, b);
-        }
-    }
-}
 
 // Gather the V2C message q = L_qn - L_rmn(old) of edge `en` at check i.
 template <typename M>
@@ -265,10 +125,6 @@ __device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float 
     } else {
         fr.post[v] = q + rn;
     }
-}
-
-__device__ __forceinline__ float u_of(float q) {
-    return ex2_ftz(-kLog2e * fminf(fabsf(q), kClipMax));
 }
 
 // Rows of degree D <= 4 use one thread per check.  Each thread first gathers

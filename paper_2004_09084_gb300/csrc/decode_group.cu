@@ -1,0 +1,724 @@
+// Frame-interleaved, clustered layered BP decoder (arXiv 2004.09084, Methods,
+// steps 1-4) for GB300 (sm_103a).
+//
+// The per-frame kernel of decode.cu gives one CTA a whole frame; every access
+// there is a 4- or 8-byte request, and the SM's rate of such requests, not
+// DRAM, bounds it.  This kernel stores the frames of a group of four side by
+// side -- the four frames' values of one variable (or message, or syndrome
+// bit) form one 16-byte word -- so that every posterior, message and channel
+// access is a single aligned 16-byte request whatever the circulant shift,
+// and one thread computes one check for four frames.
+//
+//  * Mapping: a thread-block cluster of C CTAs owns a group of four frames;
+//    CTA r of the cluster owns the checks [r Zc, (r + 1) Zc) of every row
+//    (Zc = ceil(Z / C)).  Rows of one layer share no column, so a layer needs
+//    no synchronisation inside; between layers the posteriors written by one
+//    CTA are read by others, so a layer ends with one cluster barrier
+//    (barrier.cluster arrive.release / wait.acquire).  Cross-CTA data are
+//    read through L2 only (cp.async.cg, ld.global.cg).
+//  * Layouts in library scratch, per group g: channel LLRs [n] float4,
+//    syndrome bits [m] as four bytes, core posteriors [core_cols][Z] float4,
+//    messages [slots][Z] as four FP32 (16 B) or four 16-bit values (8 B).  The
+//    kernel builds the interleaved channel and syndrome from the caller's
+//    frame-major arrays in its prologue and writes the caller's frame-major
+//    outputs in its epilogue.  Degree-1 columns keep no state (their
+//    q = L_qn - L_rmn(old) is the channel LLR exactly); in the last iteration
+//    their posterior replaces the interleaved channel value, which only their
+//    own check reads.
+//  * Rows of degree <= 4: one thread per check, operands of the next rounds
+//    copied into the thread's own shared-memory slots by cp.async while it
+//    computes the current round (no block barrier: each thread reads only the
+//    slots it filled).  Rows of degree 5..16: two lanes per check, each
+//    lane's loads issued together.
+//  * The check rule is check_rule.cuh's exclusive-product form, evaluated per
+//    frame in the same operation order as the per-frame kernel, so the two
+//    kernels give bit-identical results.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "check_rule.cuh"
+#include "qcmet_internal.h"
+
+namespace qcmet {
+
+namespace {
+
+constexpr int kGF = 4;                  // frames per group
+constexpr int kGroupMaxThreads = 512;   // launch bound (128 registers a thread)
+constexpr int kGroupMaxOps = 8;         // staged operands of a check: D <= 4 posteriors + DC messages
+#ifndef QCMET_GROUP_STAGES
+#define QCMET_GROUP_STAGES 3
+#endif
+constexpr int kGroupStages = QCMET_GROUP_STAGES;  // rounds in flight + 1
+
+extern __shared__ float4 qcmet_group_smem[];
+
+// ---- cluster primitives -------------------------------------------------------
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_nctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_idx() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives; writes before the arrive
+// (release) are visible to reads after the wait (acquire) in any CTA of it.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// ---- asynchronous copies, global -> shared, L2 only -------------------------
+__device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8_ca(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void g_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void g_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// ---- four frames' values -------------------------------------------------------
+__device__ __forceinline__ float comp(const float4 &v, int f) {
+    return f == 0 ? v.x : f == 1 ? v.y : f == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_comp(float4 &v, int f, float x) {
+    if (f == 0) v.x = x;
+    else if (f == 1) v.y = x;
+    else if (f == 2) v.z = x;
+    else v.w = x;
+}
+
+// Messages of four frames: FP32 as one float4 (16 B), 16-bit formats as four
+// packed values (8 B).
+template <typename M>
+struct MsgVec;
+
+template <>
+struct MsgVec<float> {
+    using V = float4;
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
+        cp_async16_cg(dst, src);
+    }
+    static __device__ __forceinline__ float4 from_stage(const float4 *p) { return *p; }
+    static __device__ __forceinline__ float4 load(const V *p) { return __ldcg(p); }
+    static __device__ __forceinline__ void store(V *p, const float4 &v) { *p = v; }
+};
+
+template <>
+struct MsgVec<__half> {
+    using V = uint2;
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
+        cp_async8_ca(dst, src);
+    }
+    static __device__ __forceinline__ float4 unpack(uint2 u) {
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 from_stage(const float4 *p) {
+        return unpack(*reinterpret_cast<const uint2 *>(p));
+    }
+    static __device__ __forceinline__ float4 load(const V *p) { return unpack(*p); }
+    // v holds values already rounded to half, so the conversion is exact
+    static __device__ __forceinline__ void store(V *p, const float4 &v) {
+        const __half2 a = __floats2half2_rn(v.x, v.y);
+        const __half2 b = __floats2half2_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t *>(&a);
+        u.y = *reinterpret_cast<const uint32_t *>(&b);
+        *p = u;
+    }
+};
+
+template <>
+struct MsgVec<__nv_bfloat16> {
+    using V = uint2;
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
+        cp_async8_ca(dst, src);
+    }
+    static __device__ __forceinline__ float4 unpack(uint2 u) {
+        const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+        const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+    static __device__ __forceinline__ float4 from_stage(const float4 *p) {
+        return unpack(*reinterpret_cast<const uint2 *>(p));
+    }
+    static __device__ __forceinline__ float4 load(const V *p) { return unpack(*p); }
+    static __device__ __forceinline__ void store(V *p, const float4 &v) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t *>(&a);
+        u.y = *reinterpret_cast<const uint32_t *>(&b);
+        *p = u;
+    }
+};
+
+// Sign bits of four frames' values, one per byte (the layout of a syndrome word).
+__device__ __forceinline__ uint32_t sign_bytes(const float4 &v) {
+    return (v.x < 0.0f ? 1u : 0u) | (v.y < 0.0f ? 0x100u : 0u) | (v.z < 0.0f ? 0x10000u : 0u) |
+           (v.w < 0.0f ? 0x1000000u : 0u);
+}
+
+// Views of one group's arrays.
+template <typename M>
+struct GFrame {
+    float4 *ch4;                     // [n]   channel (degree-1 posteriors after the last iteration)
+    const uint32_t *syn4;            // [m]   syndrome bit of frame f in byte f
+    float4 *core4;                   // [core_cols][Z] posteriors of the core columns
+    typename MsgVec<M>::V *msg4;     // [slots][Z] messages
+};
+
+// Rows of degree DC + D1 <= 4 (core edges first), one thread per check and
+// four frames, software-pipelined through shared memory: while a thread
+// computes round k, the operands of rounds k + 1 .. k + S - 1 are being
+// copied into its own staging slots.  Rounds of a row touch disjoint
+// variables and message slots (a circulant is a permutation), so copying later
+// rounds before round k's stores reads nothing those stores change.
+// Staging: [S rounds][D + DC operands][blockDim] 16-byte slots.
+template <int DC, int D1, typename M, int S>
+__device__ __forceinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
+                                           const GFrame<M> &fr, int lo, int hi, int Z,
+                                           bool first, bool last) {
+    constexpr int D = DC + D1;
+    constexpr int NC = DC > 0 ? DC : 1;
+    constexpr int NOP = D + DC;
+    using MV = MsgVec<M>;
+    using V = typename MV::V;
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x;
+    const uint32_t opb = (uint32_t)nt * 16u;  // bytes between operands
+    const uint32_t rb = NOP * opb;            // bytes between rounds
+    const float4 *src[D];
+    int sh[D];
+    V *slot[NC];
+#pragma unroll
+    for (int e = 0; e < D; ++e) {
+        const int4 en = ent[e];
+        src[e] = (e < DC ? fr.core4 : fr.ch4) + en.x;
+        sh[e] = en.y;
+        if (e < DC) slot[e] = fr.msg4 + (size_t)en.z * (size_t)Z;
+    }
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
+    auto issue = [&](int i, int b) {
+        if (i < hi) {
+            const uint32_t sb = s0 + (uint32_t)b * rb;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                int j = i + sh[e];
+                j = j >= Z ? j - Z : j;
+                cp_async16_cg(sb + e * opb, src[e] + j);
+            }
+            if (!first) {
+#pragma unroll
+                for (int e = 0; e < DC; ++e) MV::copy_async(sb + (D + e) * opb, slot[e] + i);
+            }
+        }
+        g_commit();
+    };
+    uint32_t sy[S];
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        const int i = lo + tid + k * nt;
+        sy[k] = i < hi ? __ldcg(fr.syn4 + check_base + i) : 0u;
+        issue(i, k);
+    }
+    int buf = 0;
+    for (int i = lo + tid; i < hi; i += nt) {
+        {
+            const int nx = i + (S - 1) * nt;
+            int nb = buf + (S - 1);
+            nb = nb >= S ? nb - S : nb;
+            sy[S - 1] = nx < hi ? __ldcg(fr.syn4 + check_base + nx) : 0u;
+            issue(nx, nb);
+        }
+        g_wait<S - 1>();
+        const float4 *sv = qcmet_group_smem + tid + (size_t)buf * (rb / 16);
+        float4 lv[D], ro[NC];
+#pragma unroll
+        for (int e = 0; e < D; ++e) lv[e] = sv[(size_t)e * nt];
+#pragma unroll
+        for (int e = 0; e < DC; ++e)
+            ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : MV::from_stage(sv + (size_t)(D + e) * nt);
+        // frame by frame; frame f's results replace its lanes of the operands
+        // (the new message in ro, the posterior q + r in lv)
+#pragma unroll
+        for (int f = 0; f < kGF; ++f) {
+            float q[D], u[D];
+            unsigned p = (sy[0] >> (8 * f)) & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const float l = comp(lv[e], f);
+                const float r = e < DC ? comp(ro[e < DC ? e : 0], f) : 0.0f;
+                q[e] = e < DC ? l - r : l;
+                p ^= q[e] < 0.0f ? 1u : 0u;
+                u[e] = u_of(q[e]);
+            }
+            exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+                if (e >= DC && !last) return;
+                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
+                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                float rn = neg ? -mag : mag;
+                if (e < DC) {
+                    rn = Msg<M>::quantize(rn);
+                    set_comp(ro[e < DC ? e : 0], f, rn);
+                }
+                set_comp(lv[e], f, q[e] + rn);
+            });
+        }
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+            if (e >= DC && !last) continue;
+            int j = i + sh[e];
+            j = j >= Z ? j - Z : j;
+            if (e < DC) MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0]);
+            const_cast<float4 *>(src[e])[j] = lv[e];
+        }
+#pragma unroll
+        for (int k = 0; k < S - 1; ++k) sy[k] = sy[k + 1];
+        buf = buf + 1 == S ? 0 : buf + 1;
+    }
+}
+
+// Rows of degree 5..16: lanes l and l ^ 16 of a warp share a check, each lane
+// owning E = ceil(D/2) edges; the lanes swap their partial products and sign
+// parities with shuffles.  A lane loads all its edges' operands (four frames
+// each) before computing; results overwrite the operands in registers and
+// are stored as whole 16-byte words.
+template <int D, typename M>
+__device__ __forceinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
+                                          const GFrame<M> &fr, int lo, int hi, int Z, bool first,
+                                          bool last) {
+    constexpr int E = (D + 1) / 2;
+    using MV = MsgVec<M>;
+    const int lane = threadIdx.x & 31;
+    const int part = lane >> 4;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int i0 = lo + warp * 16; i0 < hi; i0 += nwarps * 16) {
+        const int i = i0 + (lane & 15);
+        const bool valid = i < hi;
+        const int ic = valid ? i : hi - 1;
+        const uint32_t par4 = part == 0 ? __ldcg(fr.syn4 + check_base + ic) : 0u;
+        float4 lv[E], ro[E];
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const int e = min(part * E + el, D - 1);
+            const int4 en = ent[e];
+            int j = ic + en.y;
+            j = j >= Z ? j - Z : j;
+            lv[el] = __ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j);
+            ro[el] = (!first && en.z >= 0) ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic)
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int f = 0; f < kGF; ++f) {
+            float q[E], u[E];
+            unsigned p = (par4 >> (8 * f)) & 1u;
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const bool own = part * E + el < D;
+                q[el] = own ? comp(lv[el], f) - comp(ro[el], f) : 0.0f;
+                p ^= (own && q[el] < 0.0f) ? 1u : 0u;
+                u[el] = own ? u_of(q[el]) : 0.0f;  // 0: the identity factor I + 0 J
+            }
+            float ta = 1.0f, tb = 0.0f;
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const float na = fmaf(u[el], tb, ta);
+                const float nb = fmaf(u[el], ta, tb);
+                ta = na;
+                tb = nb;
+            }
+            const float oa = __shfl_xor_sync(0xffffffffu, ta, 16);
+            const float ob = __shfl_xor_sync(0xffffffffu, tb, 16);
+            p ^= __shfl_xor_sync(0xffffffffu, p, 16);
+            exclusive_products<E>(u, oa, ob, [&](int el, float a, float b) {
+                const int e = part * E + el;
+                if (e >= D) return;
+                const bool deg1 = ent[e].z < 0;
+                if (deg1 && !last) return;
+                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
+                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
+                const bool neg = ((p ^ (q[el] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                float rn = neg ? -mag : mag;
+                if (!deg1) {
+                    rn = Msg<M>::quantize(rn);
+                    set_comp(ro[el], f, rn);
+                }
+                set_comp(lv[el], f, q[el] + rn);
+            });
+        }
+        if (!valid) continue;
+#pragma unroll
+        for (int el = 0; el < E; ++el) {
+            const int e = part * E + el;
+            if (e >= D) continue;
+            const int4 en = ent[e];
+            if (en.z < 0 && !last) continue;
+            int j = i + en.y;
+            j = j >= Z ? j - Z : j;
+            if (en.z >= 0) {
+                MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el]);
+                fr.core4[en.x + j] = lv[el];
+            } else {
+                fr.ch4[en.x + j] = lv[el];
+            }
+        }
+    }
+}
+
+template <typename M, int S>
+__device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check_base,
+                                          const GFrame<M> &fr, int lo, int hi, int Z, bool first,
+                                          bool last) {
+    if (degree <= 4) {
+        int dc = 0;
+        for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
+        switch (degree * 8 + dc) {
+#define QCMET_GSMALL_CASE(DD, CC)                                                            \
+    case DD * 8 + CC:                                                                        \
+        grow_small<CC, DD - CC, M, S>(ent, check_base, fr, lo, hi, Z, first, last);          \
+        break;
+            QCMET_GSMALL_CASE(1, 0)
+            QCMET_GSMALL_CASE(1, 1)
+            QCMET_GSMALL_CASE(2, 0)
+            QCMET_GSMALL_CASE(2, 1)
+            QCMET_GSMALL_CASE(2, 2)
+            QCMET_GSMALL_CASE(3, 0)
+            QCMET_GSMALL_CASE(3, 1)
+            QCMET_GSMALL_CASE(3, 2)
+            QCMET_GSMALL_CASE(3, 3)
+            QCMET_GSMALL_CASE(4, 0)
+            QCMET_GSMALL_CASE(4, 1)
+            QCMET_GSMALL_CASE(4, 2)
+            QCMET_GSMALL_CASE(4, 3)
+            QCMET_GSMALL_CASE(4, 4)
+#undef QCMET_GSMALL_CASE
+            default: break;
+        }
+        return;
+    }
+    switch (degree) {
+#define QCMET_GPAIR_CASE(DD) \
+    case DD: grow_pair<DD, M>(ent, check_base, fr, lo, hi, Z, first, last); break;
+        QCMET_GPAIR_CASE(5)
+        QCMET_GPAIR_CASE(6)
+        QCMET_GPAIR_CASE(7)
+        QCMET_GPAIR_CASE(8)
+        QCMET_GPAIR_CASE(9)
+        QCMET_GPAIR_CASE(10)
+        QCMET_GPAIR_CASE(11)
+        QCMET_GPAIR_CASE(12)
+        QCMET_GPAIR_CASE(13)
+        QCMET_GPAIR_CASE(14)
+        QCMET_GPAIR_CASE(15)
+        QCMET_GPAIR_CASE(16)
+#undef QCMET_GPAIR_CASE
+        default: break;
+    }
+}
+
+// One cluster decodes frames 4g .. 4g + 3 (g = the cluster's index).  Every
+// thread of every CTA of the cluster executes the same sequence of cluster
+// barriers: one after the prologue, one per layer of every iteration and one
+// before the ok flags are written.
+template <typename M, int S>
+__global__ void __launch_bounds__(kGroupMaxThreads, 1) decode_group_kernel(const GroupArgs a) {
+    using V = typename MsgVec<M>::V;
+    const int C = (int)cluster_nctarank();
+    const int r = (int)cluster_ctarank();
+    const int g = (int)cluster_idx();
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x;
+    __shared__ unsigned s_fail;  // syndrome-test failures of the group, frame f in byte f (rank 0's)
+    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * kGroupMaxOps * nt);
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(a.image);
+        int4 *dst = reinterpret_cast<int4 *>(sw);
+        for (int k = tid; k < a.image_words / 4; k += nt) dst[k] = src[k];
+    }
+    if (tid == 0) s_fail = 0u;
+    __syncthreads();
+    const Sched s = make_sched(sw);
+    const int Z = s.Z;
+    const int Zc = (Z + C - 1) / C;
+    const int lo = min(Z, r * Zc);
+    const int hi = min(Z, lo + Zc);
+    const size_t n = (size_t)a.n, m = (size_t)a.m;
+    const int f0 = g * kGF;
+    const int nf = min(kGF, a.K - f0);
+
+    GFrame<M> fr;
+    fr.ch4 = static_cast<float4 *>(a.ch4) + (size_t)g * n;
+    fr.syn4 = a.syn4 + (size_t)g * m;
+    fr.core4 = static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * (size_t)Z;
+    fr.msg4 = static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * (size_t)Z;
+
+    // Step 1 and the interleaved copies of this CTA's share: variables
+    // [lo, hi) of every column, checks [lo, hi) of every row.  Frames past K
+    // (a partial last group) decode a channel of +1 with a zero syndrome.
+    for (int c = 0; c < s.nb; ++c) {
+        const bool core = s.col_kind[c] == kColCore;
+        const int cc = s.col_core[c];
+        const size_t cb = (size_t)c * Z;
+        for (int v = lo + tid; v < hi; v += nt) {
+            float x[kGF];
+#pragma unroll
+            for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(a.ch + (size_t)(f0 + f) * n + cb + v) : 1.0f;
+            const float4 x4 = make_float4(x[0], x[1], x[2], x[3]);
+            fr.ch4[cb + v] = x4;
+            if (core) fr.core4[(size_t)cc * Z + v] = x4;
+        }
+    }
+    for (int l = 0; l < s.mb; ++l) {
+        const size_t lb = (size_t)l * Z;
+        for (int i = lo + tid; i < hi; i += nt) {
+            uint32_t w = 0u;
+#pragma unroll
+            for (int f = 0; f < kGF; ++f)
+                if (f < nf) w |= (uint32_t)(__ldcs(a.syn + (size_t)(f0 + f) * m + lb + i) & 1u) << (8 * f);
+            const_cast<uint32_t *>(fr.syn4)[lb + i] = w;
+        }
+    }
+    cluster_sync();
+
+    // Steps 2-3: T iterations x layers; one cluster barrier per layer.
+    for (int t = 0; t < a.T; ++t) {
+        const bool first = t == 0;
+        const bool last = t == a.T - 1;
+        for (int layer = 0; layer < s.n_layers; ++layer) {
+            for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
+                const int4 row = s.rows[j];
+                gdispatch<M, S>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last);
+            }
+            cluster_sync();
+        }
+    }
+
+    // Step 4: frame-major posteriors and hard decisions of variables [lo, hi)
+    // of every column, then the syndrome test H c = s on checks [lo, hi).
+    for (int c = 0; c < s.nb; ++c) {
+        const bool core = s.col_kind[c] == kColCore;
+        const int cc = s.col_core[c];
+        const size_t cb = (size_t)c * Z;
+        for (int v = lo + tid; v < hi; v += nt) {
+            const float4 L4 = core ? __ldcg(fr.core4 + (size_t)cc * Z + v) : __ldcg(fr.ch4 + cb + v);
+#pragma unroll
+            for (int f = 0; f < kGF; ++f) {
+                if (f >= nf) break;
+                const float L = comp(L4, f);
+                if (a.post) a.post[(size_t)(f0 + f) * n + cb + v] = L;
+                a.hard[(size_t)(f0 + f) * n + cb + v] = L < 0.0f ? 1 : 0;
+            }
+        }
+    }
+    uint32_t bad = 0u;
+    for (int zr = 0; zr < s.n_zero_rows; ++zr) {
+        const size_t lb = (size_t)s.zero_rows[zr] * Z;
+        for (int i = lo + tid; i < hi; i += nt) bad |= fr.syn4[lb + i];
+    }
+    for (int j = 0; j < s.n_rows; ++j) {
+        const int4 row = s.rows[j];
+        const int4 *ent = s.entries + row.x;
+        for (int i = lo + tid; i < hi; i += nt) {
+            uint32_t p = fr.syn4[row.z + i];
+            for (int e = 0; e < row.y; ++e) {
+                const int4 en = ent[e];
+                int jj = i + en.y;
+                jj = jj >= Z ? jj - Z : jj;
+                p ^= sign_bytes(__ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + jj));
+            }
+            bad |= p;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad & 0x01010101u);
+    if ((tid & 31) == 0 && bad) {
+        uint32_t local = (uint32_t)__cvta_generic_to_shared(&s_fail);
+        uint32_t remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0));
+        asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(remote), "r"(bad)
+                     : "memory");
+    }
+    cluster_sync();
+    if (r == 0 && tid < nf) a.ok[f0 + tid] = ((s_fail >> (8 * tid)) & 1u) ? 0 : 1;
+}
+
+template <typename M>
+const void *group_kernel_ptr() {
+    return reinterpret_cast<const void *>(&decode_group_kernel<M, kGroupStages>);
+}
+
+const void *group_kernel_for(int32_t fmt) {
+    switch (fmt) {
+        case QCMET_MSG_FP32: return group_kernel_ptr<float>();
+        case QCMET_MSG_FP16: return group_kernel_ptr<__half>();
+        case QCMET_MSG_BF16: return group_kernel_ptr<__nv_bfloat16>();
+        default: return nullptr;
+    }
+}
+
+// Threads of a CTA owning `zc` checks of each row: the fewest rounds of at
+// most kGroupMaxThreads checks, spread evenly (a multiple of 32).
+int group_threads(int zc) {
+    const int rounds = (zc + kGroupMaxThreads - 1) / kGroupMaxThreads;
+    int t = (zc + rounds - 1) / rounds;
+    t = (t + 31) / 32 * 32;
+    return t < 32 ? 32 : (t > kGroupMaxThreads ? kGroupMaxThreads : t);
+}
+
+size_t group_smem(int threads, int32_t image_words) {
+    return (size_t)kGroupStages * kGroupMaxOps * threads * 16 + (size_t)image_words * sizeof(int32_t);
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return sms;
+}
+
+}  // namespace
+
+size_t group_msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 16 : 8; }
+
+int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words, int32_t want_cluster,
+                        GroupLaunch *out, std::string &err) {
+    const void *kern = group_kernel_for(fmt);
+    if (!kern) {
+        err = "unknown message format";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    const int G = (K + kGF - 1) / kGF;
+    const int sms = sm_count();
+    if (sms <= 0) {
+        err = "no CUDA device";
+        return QCMET_ERR_CUDA;
+    }
+    // candidate cluster sizes: the requested one, else 1, 2, 4, 8 with at
+    // least 128 checks per CTA
+    int cands[4], nc = 0;
+    if (want_cluster > 0) {
+        cands[nc++] = want_cluster;
+    } else {
+        for (int c = 1; c <= 8; c *= 2)
+            if (c == 1 || (Z + c - 1) / c >= 128) cands[nc++] = c;
+    }
+    double best = 0.0;
+    bool have = false;
+    for (int k = 0; k < nc; ++k) {
+        const int C = cands[k];
+        const int zc = (Z + C - 1) / C;
+        const int threads = group_threads(zc);
+        const size_t smem = group_smem(threads, image_words);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) {
+            err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+            return QCMET_ERR_UNSUPPORTED;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(G * C));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+        if (e != cudaSuccess || active <= 0) {
+            cudaGetLastError();
+            if (want_cluster > 0) {
+                err = "cluster size " + std::to_string(C) + " cannot be scheduled with " +
+                      std::to_string(smem) + " bytes of shared memory per block";
+                return QCMET_ERR_UNSUPPORTED;
+            }
+            continue;
+        }
+        // decode time ~ waves of clusters x checks per CTA
+        const int waves = (G + active - 1) / active;
+        const double cost = (double)waves * (double)((Z + C - 1) / C);
+        if (!have || cost < best * 0.999) {
+            best = cost;
+            have = true;
+            out->cluster = C;
+            out->threads = threads;
+            out->smem = smem;
+            out->groups = G;
+            out->active_clusters = active;
+        }
+    }
+    if (!have) {
+        err = "no cluster size can be scheduled on this device";
+        return QCMET_ERR_UNSUPPORTED;
+    }
+    (void)sms;
+    return QCMET_OK;
+}
+
+int launch_decode_group(const GroupArgs &a, int32_t fmt, const GroupLaunch &L, void *stream,
+                        std::string &err, size_t window_bytes, float hit_ratio) {
+    const void *kern = group_kernel_for(fmt);
+    if (!kern) {
+        err = "unknown message format";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
+    if (e != cudaSuccess) {
+        err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return QCMET_ERR_UNSUPPORTED;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(L.groups * L.cluster));
+    cfg.blockDim = dim3((unsigned)L.threads);
+    cfg.dynamicSmemBytes = L.smem;
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)L.cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    int na = 1;
+    if (window_bytes > 0) {
+        attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+        attr[1].val.accessPolicyWindow.base_ptr = a.core4;
+        attr[1].val.accessPolicyWindow.num_bytes = window_bytes;
+        attr[1].val.accessPolicyWindow.hitRatio = hit_ratio;
+        attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        na = 2;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    void *args[] = {const_cast<GroupArgs *>(&a)};
+    e = cudaLaunchKernelExC(&cfg, kern, args);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("grouped decode launch: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    return QCMET_OK;
+}
+
+}  // namespace qcmet

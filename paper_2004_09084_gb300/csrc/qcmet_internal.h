@@ -113,6 +113,10 @@ struct Code {
     // staging buffers of qcmet_decode_host
     void *d_io = nullptr;
     size_t io_bytes = 0;
+    // grouped (frame-interleaved, clustered) decode: interleaved channel,
+    // syndrome, core posteriors and messages of ceil(K/4) groups
+    void *d_group = nullptr;
+    size_t group_bytes = 0;
     // learned min-sum: scratch and the arguments of the last training forward
     void *d_learned = nullptr;
     size_t learned_bytes = 0;
@@ -197,6 +201,42 @@ int launch_decode_batch(const BatchArgs &b, int32_t msg_format, int32_t threads,
 int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void *stream,
                   std::string &err, size_t window_bytes = 0, float hit_ratio = 0.0f,
                   const CheckRule &rule = CheckRule());
+
+// Arguments of the grouped decode kernel (decode_group.cu): frames 4g .. 4g+3
+// form group g and are stored interleaved, one 16-byte word per variable.
+struct GroupArgs {
+    const float *ch;         // [K][n] caller's channel LLRs (frame-major)
+    const uint8_t *syn;      // [K][m] caller's syndromes
+    float *post;             // [K][n] output posteriors, or nullptr
+    uint8_t *hard;           // [K][n]
+    uint8_t *ok;             // [K]
+    void *ch4;               // [G][n] float4: interleaved channel (scratch)
+    uint32_t *syn4;          // [G][m]: syndrome bit of frame f in byte f (scratch)
+    void *core4;             // [G][core_cols][Z] float4: core posteriors (scratch)
+    void *msgs4;             // [G][msg_slots][Z] messages, 16 B (FP32) or 8 B (16-bit) (scratch)
+    const int32_t *image;    // schedule image (device)
+    int32_t image_words;
+    int32_t K, T, n, m, core_cols, msg_slots;
+};
+
+// Launch shape of the grouped kernel: `groups` clusters of `cluster` CTAs.
+struct GroupLaunch {
+    int32_t cluster = 0;
+    int32_t threads = 0;
+    int32_t groups = 0;
+    int32_t active_clusters = 0;  // clusters of this shape the device holds at once
+    size_t smem = 0;
+};
+
+// Bytes of one group's message for one check and slot (four frames).
+size_t group_msg_bytes(int32_t msg_format);
+// Pick the cluster size (want_cluster > 0 forces it) and block size for K
+// frames of a code with expansion Z.
+int choose_group_launch(int32_t msg_format, int32_t K, int32_t Z, int32_t image_words,
+                        int32_t want_cluster, GroupLaunch *out, std::string &err);
+int launch_decode_group(const GroupArgs &a, int32_t msg_format, const GroupLaunch &L,
+                        void *stream, std::string &err, size_t window_bytes = 0,
+                        float hit_ratio = 0.0f);
 
 // Launch the FP32 decode kernel with its messages and layer table in the
 // library's static device scratch (decode.cu): no device allocation.
