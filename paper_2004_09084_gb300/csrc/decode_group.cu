@@ -47,12 +47,6 @@ namespace qcmet {
 namespace {
 
 constexpr int kGF = 4;                  // frames per group
-constexpr int kGroupMaxThreads = 512;   // launch bound (128 registers a thread)
-constexpr int kGroupMaxOps = 8;         // staged operands of a check: D <= 4 posteriors + DC messages
-#ifndef QCMET_GROUP_STAGES
-#define QCMET_GROUP_STAGES 3
-#endif
-constexpr int kGroupStages = QCMET_GROUP_STAGES;  // rounds in flight + 1
 
 extern __shared__ float4 qcmet_group_smem[];
 
@@ -441,8 +435,13 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
 // thread of every CTA of the cluster executes the same sequence of cluster
 // barriers: one after the prologue, one per layer of every iteration and one
 // before the ok flags are written.
-template <typename M, int S>
-__global__ void __launch_bounds__(kGroupMaxThreads, 1) decode_group_kernel(const GroupArgs a) {
+//   S    : rounds staged per thread (S - 1 in flight while one is computed)
+//   NT   : largest block (launch bound); MINB: blocks per SM the bound asks for
+// Shared memory: the staging area, S * stage_ops * blockDim 16-byte slots
+// (stage_ops = the most operands a check of a row of degree <= 4 stages),
+// then the layer table.
+template <typename M, int S, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
     using V = typename MsgVec<M>::V;
     const int C = (int)cluster_nctarank();
     const int r = (int)cluster_ctarank();
@@ -450,7 +449,7 @@ __global__ void __launch_bounds__(kGroupMaxThreads, 1) decode_group_kernel(const
     const int nt = blockDim.x;
     const int tid = threadIdx.x;
     __shared__ unsigned s_fail;  // syndrome-test failures of the group, frame f in byte f (rank 0's)
-    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * kGroupMaxOps * nt);
+    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * a.stage_ops * nt);
     {
         const int4 *src = reinterpret_cast<const int4 *>(a.image);
         int4 *dst = reinterpret_cast<int4 *>(sw);
@@ -562,57 +561,62 @@ __global__ void __launch_bounds__(kGroupMaxThreads, 1) decode_group_kernel(const
     if (r == 0 && tid < nf) a.ok[f0 + tid] = ((s_fail >> (8 * tid)) & 1u) ? 0 : 1;
 }
 
-template <typename M>
-const void *group_kernel_ptr() {
-    return reinterpret_cast<const void *>(&decode_group_kernel<M, kGroupStages>);
+// Launch variants of the kernel: (rounds staged, block bound, blocks per SM).
+struct Variant {
+    int S, NT, MINB;
+    const void *kern[3];  // by message format
+};
+
+template <int S, int NT, int MINB>
+Variant make_variant() {
+    return Variant{S, NT, MINB,
+                   {reinterpret_cast<const void *>(&decode_group_kernel<float, S, NT, MINB>),
+                    reinterpret_cast<const void *>(&decode_group_kernel<__half, S, NT, MINB>),
+                    reinterpret_cast<const void *>(&decode_group_kernel<__nv_bfloat16, S, NT, MINB>)}};
 }
 
-const void *group_kernel_for(int32_t fmt) {
-    switch (fmt) {
-        case QCMET_MSG_FP32: return group_kernel_ptr<float>();
-        case QCMET_MSG_FP16: return group_kernel_ptr<__half>();
-        case QCMET_MSG_BF16: return group_kernel_ptr<__nv_bfloat16>();
-        default: return nullptr;
-    }
+const Variant *variants(int *count) {
+    static const Variant v[] = {
+        make_variant<3, 512, 1>(),
+        make_variant<4, 512, 1>(),
+        make_variant<3, 256, 2>(),
+        make_variant<4, 256, 2>(),
+    };
+    *count = (int)(sizeof(v) / sizeof(v[0]));
+    return v;
 }
 
 // Threads of a CTA owning `zc` checks of each row: the fewest rounds of at
-// most kGroupMaxThreads checks, spread evenly (a multiple of 32).
-int group_threads(int zc) {
-    const int rounds = (zc + kGroupMaxThreads - 1) / kGroupMaxThreads;
+// most `nt_max` checks, spread evenly (a multiple of 32).
+int group_threads(int zc, int nt_max) {
+    const int rounds = (zc + nt_max - 1) / nt_max;
     int t = (zc + rounds - 1) / rounds;
     t = (t + 31) / 32 * 32;
-    return t < 32 ? 32 : (t > kGroupMaxThreads ? kGroupMaxThreads : t);
+    return t < 32 ? 32 : (t > nt_max ? nt_max : t);
 }
 
-size_t group_smem(int threads, int32_t image_words) {
-    return (size_t)kGroupStages * kGroupMaxOps * threads * 16 + (size_t)image_words * sizeof(int32_t);
-}
-
-int sm_count() {
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    return sms;
+size_t group_smem(int S, int threads, int32_t stage_ops, int32_t image_words) {
+    return (size_t)S * stage_ops * threads * 16 + (size_t)image_words * sizeof(int32_t);
 }
 
 }  // namespace
 
 size_t group_msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 16 : 8; }
 
-int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words, int32_t want_cluster,
-                        GroupLaunch *out, std::string &err) {
-    const void *kern = group_kernel_for(fmt);
-    if (!kern) {
+#ifndef QCMET_GROUP_VARIANT
+#define QCMET_GROUP_VARIANT (-1)
+#endif
+
+int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
+                        int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
+                        std::string &err) {
+    if (fmt != QCMET_MSG_FP32 && fmt != QCMET_MSG_FP16 && fmt != QCMET_MSG_BF16) {
         err = "unknown message format";
         return QCMET_ERR_INVALID_ARG;
     }
     const int G = (K + kGF - 1) / kGF;
-    const int sms = sm_count();
-    if (sms <= 0) {
-        err = "no CUDA device";
-        return QCMET_ERR_CUDA;
-    }
+    int nv = 0;
+    const Variant *var = variants(&nv);
     // candidate cluster sizes: the requested one, else 1, 2, 4, 8 with at
     // least 128 checks per CTA
     int cands[4], nc = 0;
@@ -624,66 +628,75 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words, 
     }
     double best = 0.0;
     bool have = false;
-    for (int k = 0; k < nc; ++k) {
-        const int C = cands[k];
-        const int zc = (Z + C - 1) / C;
-        const int threads = group_threads(zc);
-        const size_t smem = group_smem(threads, image_words);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) {
-            err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
-            return QCMET_ERR_UNSUPPORTED;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(G * C));
-        cfg.blockDim = dim3((unsigned)threads);
-        cfg.dynamicSmemBytes = smem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int active = 0;
-        e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
-        if (e != cudaSuccess || active <= 0) {
-            cudaGetLastError();
-            if (want_cluster > 0) {
-                err = "cluster size " + std::to_string(C) + " cannot be scheduled with " +
-                      std::to_string(smem) + " bytes of shared memory per block";
-                return QCMET_ERR_UNSUPPORTED;
+    for (int vi = 0; vi < nv; ++vi) {
+        if (QCMET_GROUP_VARIANT >= 0 && vi != QCMET_GROUP_VARIANT) continue;
+        const void *kern = var[vi].kern[fmt];
+        for (int k = 0; k < nc; ++k) {
+            const int C = cands[k];
+            const int zc = (Z + C - 1) / C;
+            const int threads = group_threads(zc, var[vi].NT);
+            const size_t smem = group_smem(var[vi].S, threads, stage_ops, image_words);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
             }
-            continue;
-        }
-        // decode time ~ waves of clusters x checks per CTA
-        const int waves = (G + active - 1) / active;
-        const double cost = (double)waves * (double)((Z + C - 1) / C);
-        if (!have || cost < best * 0.999) {
-            best = cost;
-            have = true;
-            out->cluster = C;
-            out->threads = threads;
-            out->smem = smem;
-            out->groups = G;
-            out->active_clusters = active;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(G * C));
+            cfg.blockDim = dim3((unsigned)threads);
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int active = 0;
+            e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+            if (e != cudaSuccess || active <= 0) {
+                cudaGetLastError();
+                continue;
+            }
+            // decode time ~ waves of clusters x rounds per row; a second
+            // block per SM hides part of the other's latency (counted as 0.8
+            // of its rounds)
+            const int waves = (G + active - 1) / active;
+            const int rounds = (zc + threads - 1) / threads;
+            const double per_round = var[vi].MINB > 1 ? 0.8 * threads / 512.0 : threads / 512.0;
+            const double cost = (double)waves * rounds * per_round + 1e-3 * vi;
+            if (!have || cost < best) {
+                best = cost;
+                have = true;
+                out->cluster = C;
+                out->threads = threads;
+                out->groups = G;
+                out->active_clusters = active;
+                out->smem = smem;
+                out->variant = vi;
+                out->stage_ops = stage_ops;
+            }
         }
     }
     if (!have) {
-        err = "no cluster size can be scheduled on this device";
+        err = want_cluster > 0 ? "cluster size " + std::to_string(want_cluster) +
+                                     " cannot be scheduled on this device"
+                               : "no cluster size can be scheduled on this device";
         return QCMET_ERR_UNSUPPORTED;
     }
-    (void)sms;
     return QCMET_OK;
 }
 
 int launch_decode_group(const GroupArgs &a, int32_t fmt, const GroupLaunch &L, void *stream,
                         std::string &err, size_t window_bytes, float hit_ratio) {
-    const void *kern = group_kernel_for(fmt);
-    if (!kern) {
-        err = "unknown message format";
+    int nv = 0;
+    const Variant *var = variants(&nv);
+    if (fmt < 0 || fmt > 2 || L.variant < 0 || L.variant >= nv || a.stage_ops != L.stage_ops) {
+        err = "invalid grouped launch";
         return QCMET_ERR_INVALID_ARG;
     }
+    const void *kern = var[L.variant].kern[fmt];
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);

@@ -217,6 +217,7 @@ struct GroupArgs {
     const int32_t *image;    // schedule image (device)
     int32_t image_words;
     int32_t K, T, n, m, core_cols, msg_slots;
+    int32_t stage_ops;       // most operands staged per check (rows of degree <= 4)
 };
 
 // Launch shape of the grouped kernel: `groups` clusters of `cluster` CTAs.
@@ -225,15 +226,18 @@ struct GroupLaunch {
     int32_t threads = 0;
     int32_t groups = 0;
     int32_t active_clusters = 0;  // clusters of this shape the device holds at once
+    int32_t variant = 0;          // kernel build (rounds staged, block bound, blocks per SM)
+    int32_t stage_ops = 0;
     size_t smem = 0;
 };
 
 // Bytes of one group's message for one check and slot (four frames).
 size_t group_msg_bytes(int32_t msg_format);
-// Pick the cluster size (want_cluster > 0 forces it) and block size for K
-// frames of a code with expansion Z.
+// Pick the cluster size (want_cluster > 0 forces it), kernel build and block
+// size for K frames of a code with expansion Z.
 int choose_group_launch(int32_t msg_format, int32_t K, int32_t Z, int32_t image_words,
-                        int32_t want_cluster, GroupLaunch *out, std::string &err);
+                        int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
+                        std::string &err);
 int launch_decode_group(const GroupArgs &a, int32_t msg_format, const GroupLaunch &L,
                         void *stream, std::string &err, size_t window_bytes = 0,
                         float hit_ratio = 0.0f);
