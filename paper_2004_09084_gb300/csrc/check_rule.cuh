@@ -159,4 +159,101 @@ __device__ __forceinline__ float u_of(float q) {
     return ex2_ftz(-kLog2e * fminf(fabsf(q), kClipMax));
 }
 
+// ---- two frames at once ---------------------------------------------------------
+//
+// Two FP32 values in one 64-bit register pair.  The .f32x2 forms of add, sub,
+// mul and fma (sm_100 and later) apply the IEEE operation to each lane, so a
+// packed evaluation rounds exactly as two scalar ones: kernels that keep
+// several frames per thread run the rule on pairs of frames and still give
+// the results of the scalar code bit for bit.
+struct f2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float lo, float hi) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ f2 f2_splat(float x) { return f2_make(x, x); }
+__device__ __forceinline__ float f2_lo(f2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return hi;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+// a * b + c, rounded once per lane (fmaf)
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// exclusive_products on two frames at once: the same operations in the same
+// order, lane by lane (keep the two in step).
+template <int E, typename Emit>
+__device__ __forceinline__ void exclusive_products2(const f2 (&u)[E], f2 oa, f2 ob, Emit &&emit) {
+    if constexpr (E <= 6) {
+        f2 pa[E], pb[E];
+        pa[0] = oa;
+        pb[0] = ob;
+#pragma unroll
+        for (int e = 1; e < E; ++e) {
+            pa[e] = f2_fma(u[e - 1], pb[e - 1], pa[e - 1]);
+            pb[e] = f2_fma(u[e - 1], pa[e - 1], pb[e - 1]);
+        }
+        f2 sa = f2_splat(1.0f), sb = f2_splat(0.0f);
+#pragma unroll
+        for (int e = E - 1; e >= 0; --e) {
+            // cmul(pa, pb, sa, sb)
+            const f2 a = f2_fma(pa[e], sa, f2_mul(pb[e], sb));
+            const f2 b = f2_fma(pa[e], sb, f2_mul(pb[e], sa));
+            const f2 nsa = f2_fma(u[e], sb, sa);
+            const f2 nsb = f2_fma(u[e], sa, sb);
+            sa = nsa;
+            sb = nsb;
+            emit(e, a, b);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            f2 a = oa, b = ob;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                if (k == e) continue;
+                const f2 na = f2_fma(u[k], b, a);
+                const f2 nb = f2_fma(u[k], a, b);
+                a = na;
+                b = nb;
+            }
+            emit(e, a, b);
+        }
+    }
+}
+
+// u_of on two frames: |q| clipped per lane, the scaling packed, exp2 per lane.
+__device__ __forceinline__ f2 u_of2(float q0, float q1) {
+    const f2 t = f2_mul(f2_splat(-kLog2e),
+                        f2_make(fminf(fabsf(q0), kClipMax), fminf(fabsf(q1), kClipMax)));
+    return f2_make(ex2_ftz(f2_lo(t)), ex2_ftz(f2_hi(t)));
+}
+
 }  // namespace qcmet

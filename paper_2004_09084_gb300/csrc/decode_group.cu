@@ -98,6 +98,39 @@ __device__ __forceinline__ void set_comp(float4 &v, int f, float x) {
     else v.w = x;
 }
 
+// Frames (0, 1) and (2, 3) of a float4 as packed pairs.
+__device__ __forceinline__ f2 half_of(const float4 &v, int h) {
+    return h == 0 ? f2_make(v.x, v.y) : f2_make(v.z, v.w);
+}
+__device__ __forceinline__ void set_half(float4 &v, int h, f2 x) {
+    if (h == 0) {
+        v.x = f2_lo(x);
+        v.y = f2_hi(x);
+    } else {
+        v.z = f2_lo(x);
+        v.w = f2_hi(x);
+    }
+}
+
+// The new message and posterior of edge e for a pair of frames, from the
+// exclusive products (a, b) (check_rule.cuh): |r| = ln(a / b) clipped to
+// [Phi(30), 30], the sign from the parities p0, p1 (syndrome and the other
+// edges' signs), 16-bit formats rounded; returns r and writes q + r.
+template <typename M>
+__device__ __forceinline__ f2 emit_pair(f2 a, f2 b, f2 q, unsigned p0, unsigned p1, f2 &post) {
+    const f2 d = f2_sub(f2_make(lg2_ftz(f2_lo(a)), lg2_ftz(f2_hi(a))),
+                        f2_make(lg2_ftz(f2_lo(b)), lg2_ftz(f2_hi(b))));
+    const f2 mag = f2_mul(f2_splat(kLn2), d);
+    const float m0 = fminf(fmaxf(f2_lo(mag), kClipMin), kClipMax);
+    const float m1 = fminf(fmaxf(f2_hi(mag), kClipMin), kClipMax);
+    const float q0 = f2_lo(q), q1 = f2_hi(q);
+    const bool n0 = ((p0 ^ (q0 < 0.0f ? 1u : 0u)) & 1u) != 0u;
+    const bool n1 = ((p1 ^ (q1 < 0.0f ? 1u : 0u)) & 1u) != 0u;
+    const f2 r = f2_make(Msg<M>::quantize(n0 ? -m0 : m0), Msg<M>::quantize(n1 ? -m1 : m1));
+    post = f2_add(q, r);
+    return r;
+}
+
 // Messages of four frames: FP32 as one float4 (16 B), 16-bit formats as four
 // packed values (8 B).
 template <typename M>
@@ -187,10 +220,13 @@ struct GFrame {
 // variables and message slots (a circulant is a permutation), so copying later
 // rounds before round k's stores reads nothing those stores change.
 // Staging: [S rounds][D + DC operands][blockDim] 16-byte slots.
+// (Each row routine is its own function: it runs once per row and layer, and
+// a separate register allocation keeps the rows that a code rarely has from
+// costing the others spills.)
 template <int DC, int D1, typename M, int S>
-__device__ __forceinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
-                                           const GFrame<M> &fr, int lo, int hi, int Z,
-                                           bool first, bool last) {
+__device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
+                                        const GFrame<M> fr, int lo, int hi, int Z, bool first,
+                                        bool last) {
     constexpr int D = DC + D1;
     constexpr int NC = DC > 0 ? DC : 1;
     constexpr int NOP = D + DC;
@@ -251,31 +287,28 @@ __device__ __forceinline__ void grow_small(const int4 *__restrict__ ent, int che
 #pragma unroll
         for (int e = 0; e < DC; ++e)
             ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : MV::from_stage(sv + (size_t)(D + e) * nt);
-        // frame by frame; frame f's results replace its lanes of the operands
-        // (the new message in ro, the posterior q + r in lv)
+        // two frames at a time (packed); their results replace their lanes of
+        // the operands (the new message in ro, the posterior q + r in lv)
 #pragma unroll
-        for (int f = 0; f < kGF; ++f) {
-            float q[D], u[D];
-            unsigned p = (sy[0] >> (8 * f)) & 1u;
+        for (int h = 0; h < 2; ++h) {
+            f2 q[D], u[D];
+            unsigned p0 = (sy[0] >> (16 * h)) & 1u;
+            unsigned p1 = (sy[0] >> (16 * h + 8)) & 1u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                const float l = comp(lv[e], f);
-                const float r = e < DC ? comp(ro[e < DC ? e : 0], f) : 0.0f;
-                q[e] = e < DC ? l - r : l;
-                p ^= q[e] < 0.0f ? 1u : 0u;
-                u[e] = u_of(q[e]);
+                const f2 l = half_of(lv[e], h);
+                q[e] = e < DC ? f2_sub(l, half_of(ro[e < DC ? e : 0], h)) : l;
+                const float q0 = f2_lo(q[e]), q1 = f2_hi(q[e]);
+                p0 ^= q0 < 0.0f ? 1u : 0u;
+                p1 ^= q1 < 0.0f ? 1u : 0u;
+                u[e] = u_of2(q0, q1);
             }
-            exclusive_products<D>(u, 1.0f, 0.0f, [&](int e, float a, float b) {
+            exclusive_products2<D>(u, f2_splat(1.0f), f2_splat(0.0f), [&](int e, f2 a, f2 b) {
                 if (e >= DC && !last) return;
-                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
-                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
-                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
-                float rn = neg ? -mag : mag;
-                if (e < DC) {
-                    rn = Msg<M>::quantize(rn);
-                    set_comp(ro[e < DC ? e : 0], f, rn);
-                }
-                set_comp(lv[e], f, q[e] + rn);
+                f2 post;
+                const f2 r = emit_pair<M>(a, b, q[e], p0, p1, post);
+                if (e < DC) set_half(ro[e < DC ? e : 0], h, r);
+                set_half(lv[e], h, post);
             });
         }
 #pragma unroll
@@ -298,9 +331,9 @@ __device__ __forceinline__ void grow_small(const int4 *__restrict__ ent, int che
 // each) before computing; results overwrite the operands in registers and
 // are stored as whole 16-byte words.
 template <int D, typename M>
-__device__ __forceinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
-                                          const GFrame<M> &fr, int lo, int hi, int Z, bool first,
-                                          bool last) {
+__device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
+                                       const GFrame<M> fr, int lo, int hi, int Z, bool first,
+                                       bool last) {
     constexpr int E = (D + 1) / 2;
     using MV = MsgVec<M>;
     const int lane = threadIdx.x & 31;
@@ -324,41 +357,42 @@ __device__ __forceinline__ void grow_pair(const int4 *__restrict__ ent, int chec
                                            : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
-        for (int f = 0; f < kGF; ++f) {
-            float q[E], u[E];
-            unsigned p = (par4 >> (8 * f)) & 1u;
+        for (int h = 0; h < 2; ++h) {
+            f2 q[E], u[E];
+            unsigned p0 = (par4 >> (16 * h)) & 1u;
+            unsigned p1 = (par4 >> (16 * h + 8)) & 1u;
 #pragma unroll
             for (int el = 0; el < E; ++el) {
                 const bool own = part * E + el < D;
-                q[el] = own ? comp(lv[el], f) - comp(ro[el], f) : 0.0f;
-                p ^= (own && q[el] < 0.0f) ? 1u : 0u;
-                u[el] = own ? u_of(q[el]) : 0.0f;  // 0: the identity factor I + 0 J
+                q[el] = own ? f2_sub(half_of(lv[el], h), half_of(ro[el], h)) : f2_splat(0.0f);
+                const float q0 = f2_lo(q[el]), q1 = f2_hi(q[el]);
+                p0 ^= (own && q0 < 0.0f) ? 1u : 0u;
+                p1 ^= (own && q1 < 0.0f) ? 1u : 0u;
+                u[el] = own ? u_of2(q0, q1) : f2_splat(0.0f);  // 0: the identity factor I + 0 J
             }
-            float ta = 1.0f, tb = 0.0f;
+            f2 ta = f2_splat(1.0f), tb = f2_splat(0.0f);
 #pragma unroll
             for (int el = 0; el < E; ++el) {
-                const float na = fmaf(u[el], tb, ta);
-                const float nb = fmaf(u[el], ta, tb);
+                const f2 na = f2_fma(u[el], tb, ta);
+                const f2 nb = f2_fma(u[el], ta, tb);
                 ta = na;
                 tb = nb;
             }
-            const float oa = __shfl_xor_sync(0xffffffffu, ta, 16);
-            const float ob = __shfl_xor_sync(0xffffffffu, tb, 16);
-            p ^= __shfl_xor_sync(0xffffffffu, p, 16);
-            exclusive_products<E>(u, oa, ob, [&](int el, float a, float b) {
+            f2 oa, ob;
+            oa.v = __shfl_xor_sync(0xffffffffu, ta.v, 16);
+            ob.v = __shfl_xor_sync(0xffffffffu, tb.v, 16);
+            const unsigned pp = __shfl_xor_sync(0xffffffffu, p0 | (p1 << 1), 16);
+            p0 ^= pp & 1u;
+            p1 ^= pp >> 1;
+            exclusive_products2<E>(u, oa, ob, [&](int el, f2 a, f2 b) {
                 const int e = part * E + el;
                 if (e >= D) return;
                 const bool deg1 = ent[e].z < 0;
                 if (deg1 && !last) return;
-                float mag = kLn2 * (lg2_ftz(a) - lg2_ftz(b));
-                mag = fminf(fmaxf(mag, kClipMin), kClipMax);
-                const bool neg = ((p ^ (q[el] < 0.0f ? 1u : 0u)) & 1u) != 0u;
-                float rn = neg ? -mag : mag;
-                if (!deg1) {
-                    rn = Msg<M>::quantize(rn);
-                    set_comp(ro[el], f, rn);
-                }
-                set_comp(lv[el], f, q[el] + rn);
+                f2 post;
+                const f2 r = emit_pair<M>(a, b, q[el], p0, p1, post);
+                if (!deg1) set_half(ro[el], h, r);
+                set_half(lv[el], h, post);
             });
         }
         if (!valid) continue;
