@@ -171,20 +171,12 @@ struct f2 {
 };
 __device__ __forceinline__ f2 f2_make(float lo, float hi) {
     f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    r.v = ((unsigned long long)__float_as_uint(hi) << 32) | __float_as_uint(lo);
     return r;
 }
 __device__ __forceinline__ f2 f2_splat(float x) { return f2_make(x, x); }
-__device__ __forceinline__ float f2_lo(f2 a) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-    return lo;
-}
-__device__ __forceinline__ float f2_hi(f2 a) {
-    float lo, hi;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-    return hi;
-}
+__device__ __forceinline__ float f2_lo(f2 a) { return __uint_as_float((unsigned)a.v); }
+__device__ __forceinline__ float f2_hi(f2 a) { return __uint_as_float((unsigned)(a.v >> 32)); }
 __device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
     f2 r;
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));

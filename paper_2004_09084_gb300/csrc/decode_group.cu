@@ -91,12 +91,6 @@ __device__ __forceinline__ void g_wait() {
 __device__ __forceinline__ float comp(const float4 &v, int f) {
     return f == 0 ? v.x : f == 1 ? v.y : f == 2 ? v.z : v.w;
 }
-__device__ __forceinline__ void set_comp(float4 &v, int f, float x) {
-    if (f == 0) v.x = x;
-    else if (f == 1) v.y = x;
-    else if (f == 2) v.z = x;
-    else v.w = x;
-}
 
 // Frames (0, 1) and (2, 3) of a float4 as packed pairs.
 __device__ __forceinline__ f2 half_of(const float4 &v, int h) {
@@ -115,8 +109,9 @@ __device__ __forceinline__ void set_half(float4 &v, int h, f2 x) {
 // The new message and posterior of edge e for a pair of frames, from the
 // exclusive products (a, b) (check_rule.cuh): |r| = ln(a / b) clipped to
 // [Phi(30), 30], the sign from the parities p0, p1 (syndrome and the other
-// edges' signs), 16-bit formats rounded; returns r and writes q + r.
-template <typename M>
+// edges' signs); a message that is stored (an edge to a core variable) is
+// rounded to the storage format.  Returns r and writes q + r.
+template <typename M, bool Stored>
 __device__ __forceinline__ f2 emit_pair(f2 a, f2 b, f2 q, unsigned p0, unsigned p1, f2 &post) {
     const f2 d = f2_sub(f2_make(lg2_ftz(f2_lo(a)), lg2_ftz(f2_hi(a))),
                         f2_make(lg2_ftz(f2_lo(b)), lg2_ftz(f2_hi(b))));
@@ -126,7 +121,12 @@ __device__ __forceinline__ f2 emit_pair(f2 a, f2 b, f2 q, unsigned p0, unsigned 
     const float q0 = f2_lo(q), q1 = f2_hi(q);
     const bool n0 = ((p0 ^ (q0 < 0.0f ? 1u : 0u)) & 1u) != 0u;
     const bool n1 = ((p1 ^ (q1 < 0.0f ? 1u : 0u)) & 1u) != 0u;
-    const f2 r = f2_make(Msg<M>::quantize(n0 ? -m0 : m0), Msg<M>::quantize(n1 ? -m1 : m1));
+    float r0 = n0 ? -m0 : m0, r1 = n1 ? -m1 : m1;
+    if (Stored) {
+        r0 = Msg<M>::quantize(r0);
+        r1 = Msg<M>::quantize(r1);
+    }
+    const f2 r = f2_make(r0, r1);
     post = f2_add(q, r);
     return r;
 }
@@ -306,8 +306,12 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             exclusive_products2<D>(u, f2_splat(1.0f), f2_splat(0.0f), [&](int e, f2 a, f2 b) {
                 if (e >= DC && !last) return;
                 f2 post;
-                const f2 r = emit_pair<M>(a, b, q[e], p0, p1, post);
-                if (e < DC) set_half(ro[e < DC ? e : 0], h, r);
+                if (e < DC) {
+                    const f2 r = emit_pair<M, true>(a, b, q[e], p0, p1, post);
+                    set_half(ro[e < DC ? e : 0], h, r);
+                } else {
+                    emit_pair<M, false>(a, b, q[e], p0, p1, post);
+                }
                 set_half(lv[e], h, post);
             });
         }
@@ -390,8 +394,12 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
                 const bool deg1 = ent[e].z < 0;
                 if (deg1 && !last) return;
                 f2 post;
-                const f2 r = emit_pair<M>(a, b, q[el], p0, p1, post);
-                if (!deg1) set_half(ro[el], h, r);
+                if (!deg1) {
+                    const f2 r = emit_pair<M, true>(a, b, q[el], p0, p1, post);
+                    set_half(ro[el], h, r);
+                } else {
+                    emit_pair<M, false>(a, b, q[el], p0, p1, post);
+                }
                 set_half(lv[el], h, post);
             });
         }
