@@ -74,12 +74,82 @@ __device__ __forceinline__ void cluster_sync() {
         "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// ---- asynchronous copies, global -> shared, L2 only -------------------------
-__device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+// ---- memory accesses with an L2 eviction policy ---------------------------------
+//
+// Every access of the grouped kernel names an L2 policy (createpolicy): the
+// stream of each layer's messages, channel LLRs and syndrome bits, and the
+// core posteriors that every later layer reads again, can be given different
+// eviction priorities.
+#ifndef QCMET_GROUP_HINT
+#define QCMET_GROUP_HINT 0
+#endif
+struct Policies {
+    uint64_t msg;   // messages (read once and written once per iteration)
+    uint64_t in;    // interleaved channel and syndrome (read once per iteration)
+    uint64_t post;  // core posteriors (read and written by about a third of the rows)
+};
+__device__ __forceinline__ uint64_t policy_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
-__device__ __forceinline__ void cp_async8_ca(uint32_t dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+__device__ __forceinline__ uint64_t policy_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ Policies make_policies() {
+    Policies p;
+    p.msg = QCMET_GROUP_HINT >= 1 ? policy_first() : policy_normal();
+    p.in = QCMET_GROUP_HINT >= 2 ? policy_first() : policy_normal();
+    p.post = QCMET_GROUP_HINT >= 3 ? policy_last() : policy_normal();
+    return p;
+}
+
+// global -> shared copies, through L2 only (16 B) or L1 (8 B)
+__device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void *src, uint64_t pol) {
+    asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(dst),
+                 "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8_ca(uint32_t dst, const void *src, uint64_t pol) {
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(dst),
+                 "l"(src), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float4 ld16(const float4 *p, uint64_t pol) {
+    float4 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint2 ld8(const uint2 *p, uint64_t pol) {
+    uint2 v;
+    asm volatile("ld.global.cg.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
+                 : "=r"(v.x), "=r"(v.y)
+                 : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld4(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm volatile("ld.global.cg.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void st16(float4 *p, const float4 &v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x),
+                 "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st8(uint2 *p, const uint2 &v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(v.x),
+                 "r"(v.y), "l"(pol)
+                 : "memory");
 }
 __device__ __forceinline__ void g_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -139,19 +209,21 @@ struct MsgVec;
 template <>
 struct MsgVec<float> {
     using V = float4;
-    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
-        cp_async16_cg(dst, src);
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src, uint64_t pol) {
+        cp_async16_cg(dst, src, pol);
     }
     static __device__ __forceinline__ float4 from_stage(const float4 *p) { return *p; }
-    static __device__ __forceinline__ float4 load(const V *p) { return __ldcg(p); }
-    static __device__ __forceinline__ void store(V *p, const float4 &v) { *p = v; }
+    static __device__ __forceinline__ float4 load(const V *p, uint64_t pol) { return ld16(p, pol); }
+    static __device__ __forceinline__ void store(V *p, const float4 &v, uint64_t pol) {
+        st16(p, v, pol);
+    }
 };
 
 template <>
 struct MsgVec<__half> {
     using V = uint2;
-    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
-        cp_async8_ca(dst, src);
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src, uint64_t pol) {
+        cp_async8_ca(dst, src, pol);
     }
     static __device__ __forceinline__ float4 unpack(uint2 u) {
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
@@ -161,23 +233,25 @@ struct MsgVec<__half> {
     static __device__ __forceinline__ float4 from_stage(const float4 *p) {
         return unpack(*reinterpret_cast<const uint2 *>(p));
     }
-    static __device__ __forceinline__ float4 load(const V *p) { return unpack(*p); }
+    static __device__ __forceinline__ float4 load(const V *p, uint64_t pol) {
+        return unpack(ld8(p, pol));
+    }
     // v holds values already rounded to half, so the conversion is exact
-    static __device__ __forceinline__ void store(V *p, const float4 &v) {
+    static __device__ __forceinline__ void store(V *p, const float4 &v, uint64_t pol) {
         const __half2 a = __floats2half2_rn(v.x, v.y);
         const __half2 b = __floats2half2_rn(v.z, v.w);
         uint2 u;
         u.x = *reinterpret_cast<const uint32_t *>(&a);
         u.y = *reinterpret_cast<const uint32_t *>(&b);
-        *p = u;
+        st8(p, u, pol);
     }
 };
 
 template <>
 struct MsgVec<__nv_bfloat16> {
     using V = uint2;
-    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src) {
-        cp_async8_ca(dst, src);
+    static __device__ __forceinline__ void copy_async(uint32_t dst, const V *src, uint64_t pol) {
+        cp_async8_ca(dst, src, pol);
     }
     static __device__ __forceinline__ float4 unpack(uint2 u) {
         const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
@@ -187,14 +261,16 @@ struct MsgVec<__nv_bfloat16> {
     static __device__ __forceinline__ float4 from_stage(const float4 *p) {
         return unpack(*reinterpret_cast<const uint2 *>(p));
     }
-    static __device__ __forceinline__ float4 load(const V *p) { return unpack(*p); }
-    static __device__ __forceinline__ void store(V *p, const float4 &v) {
+    static __device__ __forceinline__ float4 load(const V *p, uint64_t pol) {
+        return unpack(ld8(p, pol));
+    }
+    static __device__ __forceinline__ void store(V *p, const float4 &v, uint64_t pol) {
         const __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
         const __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
         uint2 u;
         u.x = *reinterpret_cast<const uint32_t *>(&a);
         u.y = *reinterpret_cast<const uint32_t *>(&b);
-        *p = u;
+        st8(p, u, pol);
     }
 };
 
@@ -211,6 +287,7 @@ struct GFrame {
     const uint32_t *syn4;            // [m]   syndrome bit of frame f in byte f
     float4 *core4;                   // [core_cols][Z] posteriors of the core columns
     typename MsgVec<M>::V *msg4;     // [slots][Z] messages
+    Policies pol;
 };
 
 // Rows of degree DC + D1 <= 4 (core edges first), one thread per check and
@@ -254,11 +331,12 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                cp_async16_cg(sb + e * opb, src[e] + j);
+                cp_async16_cg(sb + e * opb, src[e] + j, e < DC ? fr.pol.post : fr.pol.in);
             }
             if (!first) {
 #pragma unroll
-                for (int e = 0; e < DC; ++e) MV::copy_async(sb + (D + e) * opb, slot[e] + i);
+                for (int e = 0; e < DC; ++e)
+                    MV::copy_async(sb + (D + e) * opb, slot[e] + i, fr.pol.msg);
             }
         }
         g_commit();
@@ -267,7 +345,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) {
         const int i = lo + tid + k * nt;
-        sy[k] = i < hi ? __ldcg(fr.syn4 + check_base + i) : 0u;
+        sy[k] = i < hi ? ld4(fr.syn4 + check_base + i, fr.pol.in) : 0u;
         issue(i, k);
     }
     int buf = 0;
@@ -276,7 +354,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             const int nx = i + (S - 1) * nt;
             int nb = buf + (S - 1);
             nb = nb >= S ? nb - S : nb;
-            sy[S - 1] = nx < hi ? __ldcg(fr.syn4 + check_base + nx) : 0u;
+            sy[S - 1] = nx < hi ? ld4(fr.syn4 + check_base + nx, fr.pol.in) : 0u;
             issue(nx, nb);
         }
         g_wait<S - 1>();
@@ -320,8 +398,8 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             if (e >= DC && !last) continue;
             int j = i + sh[e];
             j = j >= Z ? j - Z : j;
-            if (e < DC) MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0]);
-            const_cast<float4 *>(src[e])[j] = lv[e];
+            if (e < DC) MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0], fr.pol.msg);
+            st16(const_cast<float4 *>(src[e]) + j, lv[e], e < DC ? fr.pol.post : fr.pol.in);
         }
 #pragma unroll
         for (int k = 0; k < S - 1; ++k) sy[k] = sy[k + 1];
@@ -348,7 +426,7 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
         const int i = i0 + (lane & 15);
         const bool valid = i < hi;
         const int ic = valid ? i : hi - 1;
-        const uint32_t par4 = part == 0 ? __ldcg(fr.syn4 + check_base + ic) : 0u;
+        const uint32_t par4 = part == 0 ? ld4(fr.syn4 + check_base + ic, fr.pol.in) : 0u;
         float4 lv[E], ro[E];
 #pragma unroll
         for (int el = 0; el < E; ++el) {
@@ -356,9 +434,11 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             const int4 en = ent[e];
             int j = ic + en.y;
             j = j >= Z ? j - Z : j;
-            lv[el] = __ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j);
-            ro[el] = (!first && en.z >= 0) ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic)
-                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+            lv[el] = ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
+                          en.z < 0 ? fr.pol.in : fr.pol.post);
+            ro[el] = (!first && en.z >= 0)
+                         ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic, fr.pol.msg)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -413,10 +493,10 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             int j = i + en.y;
             j = j >= Z ? j - Z : j;
             if (en.z >= 0) {
-                MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el]);
-                fr.core4[en.x + j] = lv[el];
+                MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el], fr.pol.msg);
+                st16(fr.core4 + en.x + j, lv[el], fr.pol.post);
             } else {
-                fr.ch4[en.x + j] = lv[el];
+                st16(fr.ch4 + en.x + j, lv[el], fr.pol.in);
             }
         }
     }
@@ -501,7 +581,11 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
     __syncthreads();
     const Sched s = make_sched(sw);
     const int Z = s.Z;
-    const int Zc = (Z + C - 1) / C;
+#ifndef QCMET_GROUP_ALIGN
+#define QCMET_GROUP_ALIGN 1
+#endif
+    // checks per CTA, a multiple of QCMET_GROUP_ALIGN
+    const int Zc = ((Z + C - 1) / C + QCMET_GROUP_ALIGN - 1) / QCMET_GROUP_ALIGN * QCMET_GROUP_ALIGN;
     const int lo = min(Z, r * Zc);
     const int hi = min(Z, lo + Zc);
     const size_t n = (size_t)a.n, m = (size_t)a.m;
@@ -513,6 +597,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
     fr.syn4 = a.syn4 + (size_t)g * m;
     fr.core4 = static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * (size_t)Z;
     fr.msg4 = static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * (size_t)Z;
+    fr.pol = make_policies();
 
     // Step 1 and the interleaved copies of this CTA's share: variables
     // [lo, hi) of every column, checks [lo, hi) of every row.  Frames past K
@@ -618,11 +703,10 @@ Variant make_variant() {
 }
 
 const Variant *variants(int *count) {
+    // (four staged rounds measured no faster than three)
     static const Variant v[] = {
         make_variant<3, 512, 1>(),
-        make_variant<4, 512, 1>(),
         make_variant<3, 256, 2>(),
-        make_variant<4, 256, 2>(),
     };
     *count = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -701,13 +785,11 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                 cudaGetLastError();
                 continue;
             }
-            // decode time ~ waves of clusters x rounds per row; a second
-            // block per SM hides part of the other's latency (counted as 0.8
-            // of its rounds)
+            // An SM moves the operands of a fixed number of checks per unit of
+            // time, so the decode takes ~ waves of clusters x checks per SM:
+            // zc per block, twice that when two blocks share an SM.
             const int waves = (G + active - 1) / active;
-            const int rounds = (zc + threads - 1) / threads;
-            const double per_round = var[vi].MINB > 1 ? 0.8 * threads / 512.0 : threads / 512.0;
-            const double cost = (double)waves * rounds * per_round + 1e-3 * vi;
+            const double cost = (double)waves * zc * var[vi].MINB + 1e-3 * vi;
             if (!have || cost < best) {
                 best = cost;
                 have = true;
