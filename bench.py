@@ -39,8 +39,15 @@ K_FRAMES = 128
 ITERS = 100
 SNR = 0.161
 BYTES_PER_EDGE = {"fp32": 16, "fp16": 12, "bf16": 12}   # per edge, frame and iteration
-PROFILE = os.path.join(ROOT, "profiles", "decode_kernel_rate0.1_Z12500_K128_T100.txt")
-KERNEL_SRC = os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", "decode.cu")
+# ncu DRAM counts of the dominant kernel, one per decode kernel
+PROFILES = {
+    "group": os.path.join(ROOT, "profiles", "decode_group_kernel_rate0.1_Z12500_K128_T100.txt"),
+    "frame": os.path.join(ROOT, "profiles", "decode_kernel_rate0.1_Z12500_K128_T100.txt"),
+}
+KERNEL_SOURCES = {
+    "group": ("decode_group.cu", "check_rule.cuh", "qcmet_internal.h"),
+    "frame": ("decode.cu", "check_rule.cuh", "qcmet_internal.h"),
+}
 
 
 def workload_name(msg: str) -> str:
@@ -57,11 +64,11 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def kernel_hash() -> str:
-    """sha256 (first 16 hex digits) of the kernel sources with // comments and
+def kernel_hash(kernel: str = "group") -> str:
+    """sha256 (first 16 hex digits) of a kernel's sources with // comments and
     blank lines removed, so that a comment edit keeps a profile valid."""
     h = hashlib.sha256()
-    for name in ("decode.cu", "qcmet_internal.h"):
+    for name in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2004_09084_gb300", "csrc", name)) as f:
             for line in f:
                 code = line.split("//", 1)[0].rstrip()
@@ -70,17 +77,18 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(kernel: str = "group"):
     """DRAM bytes per launch from the committed ncu summary, if it still matches the kernel."""
-    if not os.path.exists(PROFILE):
+    path = PROFILES[kernel]
+    if not os.path.exists(path):
         return None
     vals = {}
-    with open(PROFILE) as f:
+    with open(path) as f:
         for line in f:
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_sha256_16") != kernel_hash():
+    if vals.get("kernel_source_sha256_16") != kernel_hash(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
@@ -303,8 +311,10 @@ def run_ours(args):
     h2d = pin_llr.numel() * pin_llr.element_size() + pin_syn.numel() * pin_syn.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (pin_hard, pin_post, pin_ok))
 
-    # the committed ncu figure is for this workload with FP32 messages
-    traffic = profiled_traffic() if args.msg == "fp32" else None
+    # the committed ncu figure is for this workload with FP32 messages; the
+    # library takes the grouped kernel for it unless --kernel frame
+    kern = "frame" if args.kernel == "frame" else "group"
+    traffic = profiled_traffic(kern) if args.msg == "fp32" else None
     bits = world * K_FRAMES * n
     value = job_mbit_per_s(world, K_FRAMES, n, ms * 1e-3)
     peak, peak_kind = peaks()
@@ -334,7 +344,8 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": workload_name(args.msg), "K": K_FRAMES, "Z": Z, "n": n,
                        "iterations": ITERS, "snr": SNR, "msg": args.msg,
-                       "l2_persist": args.l2_persist,
+                       "l2_persist": args.l2_persist, "kernel": args.kernel,
+                       "cluster": args.cluster,
                        "parallelism": f"dp{world} (frames sharded, no collective)",
                        "l2": "inputs larger than L2 (message state "
                              f"{K_FRAMES * info['msg_slots'] * Z * mbytes / 1e9:.2f} GB per GPU)"},
@@ -349,11 +360,12 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} hbm_gbs",
                          "model": f"{BYTES_PER_EDGE[args.msg]} B per edge per frame per iteration",
                          "stateful_bytes_frac": state_bytes / (ms * 1e-3) / 1e9 / peak,
+                         "kernel": "decode_group_kernel" if kern == "group" else "decode_kernel",
                          "note": "the model counts every core-posterior access as DRAM traffic; "
-                                 "the L2 serves part of them, so frac can exceed 1. traffic: "
-                                 "ncu-counted DRAM bytes per launch (the persisting window "
-                                 "shows no effect under ncu); traffic_frac: those bytes over "
-                                 "the timed duration"},
+                                 "the L2 serves most of them, so frac can exceed 1. traffic: "
+                                 "ncu-counted DRAM bytes per launch (1-pass capture, caches "
+                                 "not flushed); traffic_frac: those bytes over the timed "
+                                 "duration"},
             "clocks": clocks,
         }
         if cpu:

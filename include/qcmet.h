@@ -138,7 +138,11 @@ int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *laye
  *     one group, with one cluster barrier per layer.  Sum-product rule, fixed
  *     iterations.  Scratch: ceil(K/4) * (16 n + 4 m + 16 core_columns Z +
  *     msg_slots Z (16 for FP32, 8 for 16-bit messages)) bytes.
- *  QCMET_KERNEL_AUTO (0) -- the library's choice.
+ *     The grouped kernel gives each memory access an L2 eviction priority
+ *     (the streamed messages, channel and syndrome evict first, so that the
+ *     core posteriors stay in L2) and ignores l2_persist.
+ *  QCMET_KERNEL_AUTO (0) -- the grouped kernel for fixed-iteration
+ *     sum-product decodes of at least four frames, else the frame kernel.
  */
 #define QCMET_KERNEL_AUTO 0
 #define QCMET_KERNEL_FRAME 1

@@ -30,10 +30,12 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // QCMET_KERNEL_AUTO: the grouped kernel for fixed-iteration sum-product
-// decodes of at least four frames.
+// decodes of at least four frames (measured at 128 frames of the rate-0.1
+// Z = 12500 code: 7 % faster with FP32 messages, 15-20 % with FP16); the
+// per-frame kernel otherwise.
 bool use_group_by_default(const qcmet::Code &c, int32_t K) {
     (void)c;
-    return K >= 4 && false;
+    return K >= 4;
 }
 
 size_t msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 4 : 2; }
@@ -189,12 +191,9 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
               "cudaMalloc(grouped scratch)");
     if (st) return st;
     char *p = static_cast<char *>(c.d_group);
-    size_t window = 0;
-    float hit = 0.0f;
-    if (l2p) {
-        st = l2_window(G * (size_t)c.core_cols * c.Z * 16, &window, &hit);
-        if (st) return st;
-    }
+    // the grouped kernel sets L2 eviction priorities per access; it takes no
+    // persisting window (l2_persist is accepted and ignored)
+    (void)l2p;
     qcmet::GroupArgs a;
     a.ch = llr_ch;
     a.syn = syndrome;
@@ -214,7 +213,7 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     a.core_cols = c.core_cols;
     a.msg_slots = c.msg_slots;
     a.stage_ops = stage_ops;
-    st = qcmet::launch_decode_group(a, fmt, L, stream, err, window, hit);
+    st = qcmet::launch_decode_group(a, fmt, L, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
 }
