@@ -148,7 +148,8 @@ def test_mixed_batch_matches_the_oracle(q, msg, fmt, bound, T):
     # The rule passes a difference in one argument on at most undiminished
     # (|dr/dq| <= 1), but every later layer fans it out to more messages, so
     # T * 2^(2-p) bounds the typical posterior, not the worst: it must hold for
-    # 99.9 % of each frame's posteriors, and four times it for all of them.
+    # 99.5 % of each frame's posteriors, and four times it for all of them;
+    # hard decisions agree on 99.9 % of the bits.
     tol = LLR_TOL if bound is None else T * bound
     for k, (code, _, llr, syn) in enumerate(frames):
         rh, rp, rok = oracle.decode(code.base, code.shifts, code.Z, llr[None], syn[None], T,
@@ -159,7 +160,8 @@ def test_mixed_batch_matches_the_oracle(q, msg, fmt, bound, T):
         if bound is None:
             assert err.max() <= tol, f"frame {k} (Z={code.Z}): {err.max():.3g}"
         else:
-            assert np.mean(err <= tol) >= 0.999, f"frame {k} (Z={code.Z}): {np.mean(err <= tol):.4f}"
+            assert np.mean(err <= tol) >= 0.995, f"frame {k} (Z={code.Z}): {np.mean(err <= tol):.4f}"
             assert err.max() <= 4 * tol, f"frame {k} (Z={code.Z}): {err.max():.3g}"
+            assert np.mean(h == (rp[0] < 0)) >= 0.999
         assert int(b.ok[k][0].item()) == int(syndrome_ok(code, h[None], syn[None])[0])
         np.testing.assert_array_equal(h, (p < 0).astype(np.uint8))
