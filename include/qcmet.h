@@ -311,14 +311,20 @@ int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offse
  * qcmet_batch_run replays that graph on `stream` (asynchronous).  To decode
  * new data, write it into the same input buffers and run again.
  *
- * Autotuning (autotune != 0) times, on this batch with min(iterations, 4)
- * iterations, every combination of block size (512, 1024), layer schedule
+ * Two kernels can serve a batch (the choices of qcmet_decode_options.kernel):
+ * the frame kernel, whose persistent thread blocks take frames from a work
+ * counter, and the grouped kernel, whose persistent thread-block clusters
+ * take groups of up to four frames of one code (consecutive frames of that
+ * code in the batch, stored interleaved in the plan's scratch) from a work
+ * counter.  Autotuning (autotune != 0) times, on this batch with
+ * min(iterations, 4) iterations, every combination of kernel and its size
+ * (block of 512 or 1024 threads; cluster of 2, 4 or 8 blocks), layer schedule
  * (each code's own, or the other schedule that gives identical results:
- * base-row order <-> merged rows, Results Eqs. (m1), (m2)) and frame order
+ * base-row order <-> merged rows, Results Eqs. (m1), (m2)) and work order
  * (largest first, or as given), and keeps the fastest.  All candidates give
  * the same results, so the choice affects time only.  Autotuning runs trial
  * decodes, so the inputs must be valid and the outputs writable at creation.
- * Frames are taken by persistent thread blocks from a work counter.
+ * Without autotuning the plan takes the grouped kernel with clusters of 4.
  */
 typedef struct {
     const qcmet_code *code;   /* the frame's code                          */
@@ -332,12 +338,14 @@ typedef struct {
 typedef struct qcmet_batch qcmet_batch;
 
 typedef struct {
-    int32_t threads_per_block;   /* chosen block size                                  */
+    int32_t threads_per_block;   /* frame kernel: chosen block size (0 for the grouped) */
     int32_t alternate_schedule;  /* 1: the codes' other exact schedule was faster       */
-    int32_t largest_first;       /* 1: frames are taken in decreasing edge count       */
+    int32_t largest_first;       /* 1: work is taken in decreasing edge count          */
     int32_t candidates;          /* configurations timed (1 without autotuning)        */
     float trial_ms;              /* time of two trial decodes of the winner (-1 if none) */
-    int32_t reserved[3];
+    int32_t kernel;              /* QCMET_KERNEL_FRAME or QCMET_KERNEL_GROUP            */
+    int32_t cluster_size;        /* grouped kernel: blocks per cluster (else 0)         */
+    int32_t reserved[1];
 } qcmet_batch_config;
 
 /* frames: host array [K] (copied); msg_format: QCMET_MSG_*.  Pointers must be

@@ -74,7 +74,8 @@ class Frame(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("alternate_schedule", ctypes.c_int32),
                 ("largest_first", ctypes.c_int32), ("candidates", ctypes.c_int32),
-                ("trial_ms", ctypes.c_float), ("reserved", ctypes.c_int32 * 3)]
+                ("trial_ms", ctypes.c_float), ("kernel", ctypes.c_int32),
+                ("cluster_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class DecodeOptions(ctypes.Structure):

@@ -164,18 +164,7 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
 int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                  int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok, int32_t fmt,
                  int32_t cluster, bool l2p, void *stream) {
-    // the most operands a check of a row of degree <= 4 stages: its edges'
-    // posteriors or channel LLRs plus the old messages of its core edges
-    int32_t stage_ops = 1;
-    for (int32_t l = 0; l < c.mb; ++l) {
-        int32_t d = 0, dc = 0;
-        for (int32_t col = 0; col < c.nb; ++col) {
-            if (!c.base[(size_t)l * c.nb + col]) continue;
-            ++d;
-            dc += c.col_degree[col] > 1 ? 1 : 0;
-        }
-        if (d >= 1 && d <= 4) stage_ops = std::max(stage_ops, d + dc);
-    }
+    const int32_t stage_ops = qcmet::group_stage_ops(c);
     qcmet::GroupLaunch L;
     std::string err;
     int st = qcmet::choose_group_launch(fmt, K, c.Z, (int32_t)c.image.words.size(), stage_ops,

@@ -565,56 +565,43 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
     }
 }
 
-// One cluster decodes frames 4g .. 4g + 3 (g = the cluster's index).  Every
-// thread of every CTA of the cluster executes the same sequence of cluster
-// barriers: one after the prologue, one per layer of every iteration and one
-// before the ok flags are written.
-//   S    : rounds staged per thread (S - 1 in flight while one is computed)
-//   NT   : largest block (launch bound); MINB: blocks per SM the bound asks for
-// Shared memory: the staging area, S * stage_ops * blockDim 16-byte slots
-// (stage_ops = the most operands a check of a row of degree <= 4 stages),
-// then the layer table.
-template <typename M, int S, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
-    using V = typename MsgVec<M>::V;
-    const int C = (int)cluster_nctarank();
-    const int r = (int)cluster_ctarank();
-    const int g = (int)cluster_idx();
-    const int nt = blockDim.x;
-    const int tid = threadIdx.x;
-    __shared__ unsigned s_fail;  // syndrome-test failures of the group, frame f in byte f (rank 0's)
-    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * a.stage_ops * nt);
-    {
-        const int4 *src = reinterpret_cast<const int4 *>(a.image);
-        int4 *dst = reinterpret_cast<int4 *>(sw);
-        for (int k = tid; k < a.image_words / 4; k += nt) dst[k] = src[k];
-    }
-    if (tid == 0) s_fail = 0u;
-    __syncthreads();
-    const Sched s = make_sched(sw);
-    const int Z = s.Z;
+// The frames of one group: frame f < nf reads ch[f] [n] and syn[f] [m] and
+// writes post[f] [n] (when not null), hard[f] [n] and ok[f] [1].
+struct GroupIO {
+    const float *ch[kGF];
+    const uint8_t *syn[kGF];
+    float *post[kGF];
+    uint8_t *hard[kGF];
+    uint8_t *ok[kGF];
+    int nf;
+};
+
 #ifndef QCMET_GROUP_ALIGN
 #define QCMET_GROUP_ALIGN 1
 #endif
+
+// One cluster decodes one group (steps 1-4) with the schedule `s` in shared
+// memory; CTA r of the cluster's C owns checks [lo, hi) of every row.  Every
+// thread of every CTA of the cluster executes the same sequence of cluster
+// barriers: one after the prologue, one per layer of every iteration and one
+// before the ok flags are written.  s_fail is a shared word of the calling
+// CTA (rank 0's collects the syndrome-test failures).
+template <typename M, int S>
+__device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO &io, GFrame<M> fr,
+                                                  int T, int r, int C, unsigned *s_fail) {
+    const int nt = blockDim.x;
+    const int tid = threadIdx.x;
+    const int Z = s.Z;
     // checks per CTA, a multiple of QCMET_GROUP_ALIGN
     const int Zc = ((Z + C - 1) / C + QCMET_GROUP_ALIGN - 1) / QCMET_GROUP_ALIGN * QCMET_GROUP_ALIGN;
     const int lo = min(Z, r * Zc);
     const int hi = min(Z, lo + Zc);
-    const size_t n = (size_t)a.n, m = (size_t)a.m;
-    const int f0 = g * kGF;
-    const int nf = min(kGF, a.K - f0);
-
-    GFrame<M> fr;
-    fr.ch4 = static_cast<float4 *>(a.ch4) + (size_t)g * n;
-    fr.syn4 = a.syn4 + (size_t)g * m;
-    fr.core4 = static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * (size_t)Z;
-    fr.msg4 = static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * (size_t)Z;
-    fr.pol = make_policies<std::is_same<M, float>::value ? QCMET_GROUP_HINT_FP32
-                                                          : QCMET_GROUP_HINT_16BIT>();
+    const int nf = io.nf;
+    if (r == 0 && tid == 0) *s_fail = 0u;
 
     // Step 1 and the interleaved copies of this CTA's share: variables
-    // [lo, hi) of every column, checks [lo, hi) of every row.  Frames past K
-    // (a partial last group) decode a channel of +1 with a zero syndrome.
+    // [lo, hi) of every column, checks [lo, hi) of every row.  Lanes past nf
+    // (a partial group) decode a channel of +1 with a zero syndrome.
     for (int c = 0; c < s.nb; ++c) {
         const bool core = s.col_kind[c] == kColCore;
         const int cc = s.col_core[c];
@@ -622,7 +609,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
         for (int v = lo + tid; v < hi; v += nt) {
             float x[kGF];
 #pragma unroll
-            for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(a.ch + (size_t)(f0 + f) * n + cb + v) : 1.0f;
+            for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(io.ch[f] + cb + v) : 1.0f;
             const float4 x4 = make_float4(x[0], x[1], x[2], x[3]);
             fr.ch4[cb + v] = x4;
             if (core) fr.core4[(size_t)cc * Z + v] = x4;
@@ -634,16 +621,16 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
             uint32_t w = 0u;
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
-                if (f < nf) w |= (uint32_t)(__ldcs(a.syn + (size_t)(f0 + f) * m + lb + i) & 1u) << (8 * f);
+                if (f < nf) w |= (uint32_t)(__ldcs(io.syn[f] + lb + i) & 1u) << (8 * f);
             const_cast<uint32_t *>(fr.syn4)[lb + i] = w;
         }
     }
     cluster_sync();
 
     // Steps 2-3: T iterations x layers; one cluster barrier per layer.
-    for (int t = 0; t < a.T; ++t) {
+    for (int t = 0; t < T; ++t) {
         const bool first = t == 0;
-        const bool last = t == a.T - 1;
+        const bool last = t == T - 1;
         for (int layer = 0; layer < s.n_layers; ++layer) {
             for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
                 const int4 row = s.rows[j];
@@ -665,8 +652,8 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
             for (int f = 0; f < kGF; ++f) {
                 if (f >= nf) break;
                 const float L = comp(L4, f);
-                if (a.post) a.post[(size_t)(f0 + f) * n + cb + v] = L;
-                a.hard[(size_t)(f0 + f) * n + cb + v] = L < 0.0f ? 1 : 0;
+                if (io.post[f]) io.post[f][cb + v] = L;
+                io.hard[f][cb + v] = L < 0.0f ? 1 : 0;
             }
         }
     }
@@ -691,14 +678,118 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
     }
     bad = __reduce_or_sync(0xffffffffu, bad & 0x01010101u);
     if ((tid & 31) == 0 && bad) {
-        uint32_t local = (uint32_t)__cvta_generic_to_shared(&s_fail);
+        uint32_t local = (uint32_t)__cvta_generic_to_shared(s_fail);
         uint32_t remote;
         asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0));
         asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(remote), "r"(bad)
                      : "memory");
     }
     cluster_sync();
-    if (r == 0 && tid < nf) a.ok[f0 + tid] = ((s_fail >> (8 * tid)) & 1u) ? 0 : 1;
+    if (r == 0 && tid < nf) io.ok[tid][0] = ((*s_fail >> (8 * tid)) & 1u) ? 0 : 1;
+}
+
+template <typename M>
+__device__ __forceinline__ GFrame<M> group_scratch(void *ch4, uint32_t *syn4, void *core4,
+                                                   void *msgs4) {
+    GFrame<M> fr;
+    fr.ch4 = static_cast<float4 *>(ch4);
+    fr.syn4 = syn4;
+    fr.core4 = static_cast<float4 *>(core4);
+    fr.msg4 = static_cast<typename MsgVec<M>::V *>(msgs4);
+    fr.pol = make_policies<std::is_same<M, float>::value ? QCMET_GROUP_HINT_FP32
+                                                          : QCMET_GROUP_HINT_16BIT>();
+    return fr;
+}
+
+// Copy a code's layer table into shared memory (every thread of the block).
+__device__ __forceinline__ void load_image(int32_t *sw, const int32_t *image, int words) {
+    const int4 *src = reinterpret_cast<const int4 *>(image);
+    int4 *dst = reinterpret_cast<int4 *>(sw);
+    for (int k = threadIdx.x; k < words / 4; k += blockDim.x) dst[k] = src[k];
+}
+
+// K frames of one code: cluster g decodes frames 4g .. 4g + 3.
+//   S    : rounds staged per thread (S - 1 in flight while one is computed)
+//   NT   : largest block (launch bound); MINB: blocks per SM the bound asks for
+// Shared memory: the staging area, S * stage_ops * blockDim 16-byte slots
+// (stage_ops = the most operands a check of a row of degree <= 4 stages),
+// then the layer table.
+template <typename M, int S, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
+    using V = typename MsgVec<M>::V;
+    const int C = (int)cluster_nctarank();
+    const int r = (int)cluster_ctarank();
+    const int g = (int)cluster_idx();
+    __shared__ unsigned s_fail;
+    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * a.stage_ops * blockDim.x);
+    load_image(sw, a.image, a.image_words);
+    __syncthreads();
+    const Sched s = make_sched(sw);
+    const size_t n = (size_t)a.n, m = (size_t)a.m, Z = (size_t)s.Z;
+    const int f0 = g * kGF;
+    GroupIO io;
+    io.nf = min(kGF, a.K - f0);
+#pragma unroll
+    for (int f = 0; f < kGF; ++f) {
+        const bool have = f < io.nf;
+        io.ch[f] = have ? a.ch + (size_t)(f0 + f) * n : nullptr;
+        io.syn[f] = have ? a.syn + (size_t)(f0 + f) * m : nullptr;
+        io.post[f] = (have && a.post) ? a.post + (size_t)(f0 + f) * n : nullptr;
+        io.hard[f] = have ? a.hard + (size_t)(f0 + f) * n : nullptr;
+        io.ok[f] = have ? a.ok + f0 + f : nullptr;
+    }
+    const GFrame<M> fr = group_scratch<M>(
+        static_cast<float4 *>(a.ch4) + (size_t)g * n, a.syn4 + (size_t)g * m,
+        static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * Z,
+        static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * Z);
+    decode_group_body<M, S>(s, io, fr, a.T, r, C, &s_fail);
+}
+
+// Mixed batches: persistent clusters take groups (up to four frames of one
+// code) from an atomic counter in the order given -- a work queue, nothing
+// waits on another cluster -- reload the layer table when the code changes,
+// and decode the group.  Rank 0 takes the next job and the others read it
+// from rank 0's shared memory.
+template <typename M, int S, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const GroupBatchArgs b) {
+    const int C = (int)cluster_nctarank();
+    const int r = (int)cluster_ctarank();
+    __shared__ unsigned s_fail;
+    __shared__ int s_job;
+    int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * b.stage_ops * blockDim.x);
+    int cur_code = -1;
+    for (;;) {
+        if (r == 0 && threadIdx.x == 0) s_job = atomicAdd(b.counter, 1);
+        cluster_sync();
+        int k;
+        {
+            const uint32_t local = (uint32_t)__cvta_generic_to_shared(&s_job);
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0));
+            asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(k) : "r"(remote) : "memory");
+        }
+        cluster_sync();  // every CTA has read the job: rank 0 may overwrite it or exit
+        if (k >= b.J) break;
+        const GroupJob &jb = b.jobs[b.order[k]];
+        if (jb.code_id != cur_code) {
+            load_image(sw, jb.image, jb.image_words);
+            __syncthreads();
+            cur_code = jb.code_id;
+        }
+        const Sched s = make_sched(sw);
+        GroupIO io;
+        io.nf = jb.nf;
+#pragma unroll
+        for (int f = 0; f < kGF; ++f) {
+            io.ch[f] = jb.ch[f];
+            io.syn[f] = jb.syn[f];
+            io.post[f] = jb.post[f];
+            io.hard[f] = jb.hard[f];
+            io.ok[f] = jb.ok[f];
+        }
+        const GFrame<M> fr = group_scratch<M>(jb.ch4, jb.syn4, jb.core4, jb.msgs4);
+        decode_group_body<M, S>(s, io, fr, b.T, r, C, &s_fail);
+    }
 }
 
 // Launch variants of the kernel: (rounds staged, block bound, blocks per SM).
@@ -821,6 +912,79 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                                      " cannot be scheduled on this device"
                                : "no cluster size can be scheduled on this device";
         return QCMET_ERR_UNSUPPORTED;
+    }
+    return QCMET_OK;
+}
+
+int32_t group_stage_ops(const Code &c) {
+    int32_t ops = 1;
+    for (int32_t l = 0; l < c.mb; ++l) {
+        int32_t d = 0, dc = 0;
+        for (int32_t col = 0; col < c.nb; ++col) {
+            if (!c.base[(size_t)l * c.nb + col]) continue;
+            ++d;
+            dc += c.col_degree[col] > 1 ? 1 : 0;
+        }
+        if (d >= 1 && d <= 4) ops = d + dc > ops ? d + dc : ops;
+    }
+    return ops;
+}
+
+namespace {
+template <typename M>
+const void *group_batch_kernel_ptr() {
+    return reinterpret_cast<const void *>(&decode_group_batch_kernel<M, 3, 512, 1>);
+}
+}  // namespace
+
+int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t cluster, int32_t max_Z,
+                              int32_t max_image_words, void *stream, std::string &err) {
+    const void *kern = fmt == QCMET_MSG_FP32   ? group_batch_kernel_ptr<float>()
+                       : fmt == QCMET_MSG_FP16 ? group_batch_kernel_ptr<__half>()
+                       : fmt == QCMET_MSG_BF16 ? group_batch_kernel_ptr<__nv_bfloat16>()
+                                               : nullptr;
+    if (!kern || cluster < 1 || cluster > 8 || max_Z < 1) {
+        err = "invalid grouped batch launch";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    if (b.J <= 0) return QCMET_OK;
+    const int C = cluster;
+    const int threads = group_threads((max_Z + C - 1) / C, 512);
+    const size_t smem = group_smem(3, threads, b.stage_ops, max_image_words);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+        return QCMET_ERR_UNSUPPORTED;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = static_cast<cudaStream_t>(stream);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // persistent clusters: as many as the device holds at once, at most one per job
+    cfg.gridDim = dim3((unsigned)(b.J * C));
+    int active = 0;
+    e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+    if (e != cudaSuccess || active <= 0) {
+        cudaGetLastError();
+        err = "cluster size " + std::to_string(C) + " cannot be scheduled for this batch";
+        return QCMET_ERR_UNSUPPORTED;
+    }
+    const int clusters = active < b.J ? active : b.J;
+    cfg.gridDim = dim3((unsigned)(clusters * C));
+    void *args[] = {const_cast<GroupBatchArgs *>(&b)};
+    e = cudaLaunchKernelExC(&cfg, kern, args);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        err = std::string("grouped batch launch: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
     }
     return QCMET_OK;
 }

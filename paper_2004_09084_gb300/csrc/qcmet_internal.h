@@ -231,6 +231,44 @@ struct GroupLaunch {
     size_t smem = 0;
 };
 
+// One job of a mixed batch on the grouped kernel: up to four frames of one
+// code, stored interleaved in the job's own scratch.
+struct GroupJob {
+    const int32_t *image;    // the code's schedule image (device)
+    int32_t image_words;
+    int32_t code_id;         // jobs with equal code_id share the image
+    int32_t nf;              // frames in the group (1..4)
+    int32_t pad;
+    const float *ch[4];      // per frame [n]
+    const uint8_t *syn[4];   // per frame [m]
+    float *post[4];          // per frame [n], or nullptr
+    uint8_t *hard[4];        // per frame [n]
+    uint8_t *ok[4];          // per frame [1]
+    void *ch4;               // [n] float4
+    uint32_t *syn4;          // [m]
+    void *core4;             // [core_cols][Z] float4
+    void *msgs4;             // [msg_slots][Z] messages
+};
+
+struct GroupBatchArgs {
+    const GroupJob *jobs;    // [J]
+    const int32_t *order;    // [J] job indices in the order clusters take them
+    int32_t *counter;        // work counter (zero before the launch)
+    int32_t J, T;
+    int32_t stage_ops;       // most operands staged per check over the batch's codes
+};
+
+// One launch of the grouped batch kernel with clusters of `cluster` blocks
+// sized for expansion factors up to max_Z; -8 (UNSUPPORTED) when that cluster
+// size cannot be scheduled.
+int launch_decode_group_batch(const GroupBatchArgs &b, int32_t msg_format, int32_t cluster,
+                              int32_t max_Z, int32_t max_image_words, void *stream,
+                              std::string &err);
+
+// The most operands a check of a row of degree <= 4 stages (its edges'
+// posteriors or channel LLRs plus the old messages of its core edges).
+int32_t group_stage_ops(const Code &c);
+
 // Bytes of one group's message for one check and slot (four frames).
 size_t group_msg_bytes(int32_t msg_format);
 // Pick the cluster size (want_cluster > 0 forces it), kernel build and block

@@ -43,7 +43,12 @@ def test_batch_equals_per_code_decoding(q, msg, autotune):
     b.run()
     torch.cuda.synchronize()
     cfg = b.config()
-    assert cfg["candidates"] == (8 if autotune else 1)
+    # autotuned: frame kernel (2 block sizes) and grouped kernel (3 cluster
+    # sizes), each x 2 schedules x 2 orders; else the grouped kernel, clusters of 4
+    assert cfg["candidates"] == (20 if autotune else 1)
+    assert cfg["kernel"] in (1, 2)
+    if not autotune:
+        assert cfg["kernel"] == 2 and cfg["cluster_size"] == 4
     for k, (qc, llr, syn, x) in enumerate(frames):
         h, p, ok = q.decode(qc, llr[None].contiguous(), syn[None].contiguous(), T, msg=msg)
         torch.cuda.synchronize()
