@@ -334,7 +334,9 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
     float best_ms = -1.0f;
     int32_t timed = 0;
     if (cands.size() > 1) {
-        const int32_t Tt = std::min<int32_t>(iterations, 4);
+        // enough iterations that the per-launch work (interleaving, outputs,
+        // syndrome test) does not decide the choice
+        const int32_t Tt = std::min<int32_t>(iterations, 12);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
