@@ -526,8 +526,11 @@ def run_report(args):
                 print(json.dumps({"report": "learned", "trained_on": [lo, hi], "snr": snr,
                                   "iterations": T, **res}), flush=True)
             if args.save_weights:
-                np.savez(args.save_weights.replace(".npz", f"_{lo}_{hi}.npz"),
-                         w_scale=ws.detach().cpu().numpy(), w_offset=wo.detach().cpu().numpy())
+                # flat FP32 file + JSON header (learned.save_weights)
+                learned.save_weights(f"{args.save_weights}_{lo}_{hi}.f32", ws, wo, code.base,
+                                     code.shifts, code.Z,
+                                     info={"snr_range": [lo, hi], "frames": frames,
+                                           "batch": batch, "init_scale": args.init_scale})
         return 0
     if args.report == "batch":
         # mixed batch: 192 codewords across rates 0.1/0.05/0.02 and lengths
@@ -585,7 +588,8 @@ def main():
     ap.add_argument("--launches", type=int, default=2)
     ap.add_argument("--train-frames", type=int, default=10_000,
                     help="--report learned: training frames (decoder-generated)")
-    ap.add_argument("--save-weights", default="", help="--report learned: write weights (.npz)")
+    ap.add_argument("--save-weights", default="",
+                    help="--report learned: write the weights to <prefix>_<lo>_<hi>.f32 (+ .json)")
     ap.add_argument("--init-scale", type=float, default=0.25,
                     help="--report learned: initial min-sum scale (offsets start at 0)")
     ap.add_argument("--train-batch", type=int, default=128,

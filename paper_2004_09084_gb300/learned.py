@@ -11,9 +11,16 @@ the reference decoder.
 """
 from __future__ import annotations
 
+import hashlib
+import json
+import os
+
 import numpy as np
 
 from . import Code, _check, lib
+
+WEIGHTS_FORMAT = "qcmet-minsum-weights"
+WEIGHTS_VERSION = 1
 
 
 def _ptr(t):
@@ -121,3 +128,86 @@ def make_batch(code: Code, K: int, snr_lo: float, snr_hi: float, generator):
     y = (1.0 - 2.0 * x.float()) + noise / torch.sqrt(snr)
     llr = (2.0 * y * snr).float().contiguous()
     return llr, syn.view(K, mb * Z).contiguous(), x.contiguous()
+
+
+def code_digest(base, shifts, Z: int) -> str:
+    """sha256 of a code's description (shape, base matrix, shifts, Z): weights
+    belong to one code, so a file records which."""
+    base = np.ascontiguousarray(base, dtype=np.int8)
+    shifts = np.ascontiguousarray(np.where(base == 1, shifts, 0), dtype=np.int32)
+    h = hashlib.sha256()
+    h.update(np.asarray(base.shape, dtype=np.int64).tobytes())
+    h.update(base.tobytes())
+    h.update(shifts.astype("<i4").tobytes())
+    h.update(np.int64(Z).tobytes())
+    return h.hexdigest()
+
+
+def save_weights(path: str, w_scale, w_offset, base, shifts, Z: int, info: dict | None = None):
+    """Write learned weights as a flat FP32 file plus a JSON header.
+
+    ``path`` receives the raw little-endian float32 values of ``w_scale``
+    followed by those of ``w_offset``, each ``[iterations][mb][2]`` row-major
+    (edge type 0: edges to variables of degree > 1, 1: edges to degree-1
+    variables); ``path + ".json"`` receives the header: format, version,
+    shape, layout, byte counts, the sha256 of the data, the code it belongs to
+    (mb, nb, Z, digest of base and shifts) and ``info`` (free-form, e.g. the
+    training SNR range).  Accepts numpy arrays or tensors (any device).
+    """
+    ws = _as_numpy(w_scale)
+    wo = _as_numpy(w_offset)
+    base = np.asarray(base)
+    mb, nb = base.shape
+    if ws.shape != wo.shape or ws.ndim != 3 or ws.shape[1] != mb or ws.shape[2] != 2:
+        raise ValueError(f"weights must both have shape [iterations, {mb}, 2]")
+    data = ws.astype("<f4").tobytes() + wo.astype("<f4").tobytes()
+    header = {
+        "format": WEIGHTS_FORMAT, "version": WEIGHTS_VERSION, "dtype": "float32-le",
+        "shape": [int(ws.shape[0]), int(mb), 2],
+        "layout": "w_scale then w_offset, each [iteration][base row][edge type] row-major; "
+                  "edge type 0: to a variable of degree > 1, 1: to a degree-1 variable",
+        "bytes": len(data), "sha256": hashlib.sha256(data).hexdigest(),
+        "code": {"mb": int(mb), "nb": int(nb), "Z": int(Z), "digest": code_digest(base, shifts, Z)},
+        "info": info or {},
+    }
+    tmp = path + ".tmp"
+    with open(tmp, "wb") as f:
+        f.write(data)
+    os.replace(tmp, path)
+    with open(path + ".json", "w") as f:
+        json.dump(header, f, indent=1, sort_keys=True)
+    return header
+
+
+def load_weights(path: str, base=None, shifts=None, Z: int | None = None):
+    """Read weights written by :func:`save_weights`; returns ``(w_scale,
+    w_offset, header)`` as float32 numpy arrays.  Checks the format, the byte
+    count and the data digest, and, when the code is given, that the weights
+    belong to it; raises ValueError otherwise."""
+    with open(path + ".json") as f:
+        header = json.load(f)
+    if header.get("format") != WEIGHTS_FORMAT or header.get("version") != WEIGHTS_VERSION:
+        raise ValueError(f"{path}: not a {WEIGHTS_FORMAT} v{WEIGHTS_VERSION} file")
+    with open(path, "rb") as f:
+        data = f.read()
+    if len(data) != header["bytes"] or hashlib.sha256(data).hexdigest() != header["sha256"]:
+        raise ValueError(f"{path}: data does not match its header (size or sha256)")
+    T, mb, two = header["shape"]
+    count = T * mb * two
+    if header["bytes"] != 2 * 4 * count:
+        raise ValueError(f"{path}: byte count disagrees with the shape")
+    vals = np.frombuffer(data, dtype="<f4")
+    ws = vals[:count].reshape(T, mb, two).astype(np.float32)
+    wo = vals[count:].reshape(T, mb, two).astype(np.float32)
+    if base is not None:
+        if Z is None or shifts is None:
+            raise ValueError("give base, shifts and Z together")
+        if code_digest(base, shifts, Z) != header["code"]["digest"]:
+            raise ValueError(f"{path}: the weights belong to another code")
+    return ws, wo, header
+
+
+def _as_numpy(x):
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    return np.ascontiguousarray(x, dtype=np.float32)
