@@ -20,6 +20,13 @@
  *    never aborts or traps.  qcmet_last_error() returns a message for the
  *    last failing call of the calling thread.
  *
+ * Tracing: with the environment variable QCMET_NVTX=1 (read once, at the
+ * library's first call) the host calls push NVTX ranges in the "qcmet"
+ * domain: one per decode launch, named with its kernel, frame count and
+ * layer-group schedule (a decode runs all layer groups of all iterations in
+ * one launch), plus ranges around qcmet_decode_host, batch runs and the
+ * min-sum training calls.
+ *
  * Thread safety: distinct code handles are independent.  One handle owns
  * device scratch; calls on the same handle must not run concurrently (on two
  * host threads or on two streams that overlap on the GPU).
@@ -356,6 +363,19 @@ int qcmet_batch_run(qcmet_batch *batch, void *stream);
 int qcmet_batch_get_config(const qcmet_batch *batch, qcmet_batch_config *out);
 /* Frees the plan (not the codes or the caller's buffers).  NULL is a no-op. */
 void qcmet_batch_destroy(qcmet_batch *batch);
+
+/*
+ * Index checks of the debug build.  libqcmet_debug.so (the same sources built
+ * with QCMET_DEBUG_CHECKS=1) tests every index its kernels gather or scatter
+ * -- posteriors and channel LLRs, message slots, syndrome bits -- against the
+ * extent of its array and skips an access that would leave it, recording the
+ * kind: bit 0 a variable index, bit 1 a message slot, bit 2 a check index.
+ * This call waits for the current device to finish its work, returns the bits
+ * recorded since the last call in *violations and clears them.  The release
+ * build compiles no checks: it sets *violations = 0 and returns
+ * QCMET_ERR_UNSUPPORTED.  Errors: INVALID_ARG (NULL), CUDA.
+ */
+int qcmet_debug_checks(uint32_t *violations);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *qcmet_last_error(void);

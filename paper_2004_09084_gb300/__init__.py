@@ -21,7 +21,10 @@ import numpy as np
 
 from . import build as _build
 
-_LIB_PATH = _build.LIB
+# QCMET_DEBUG_BUILD=1 loads the debug build (every kernel index checked,
+# qcmet_debug_checks); the default is the release build
+_DEBUG = os.environ.get("QCMET_DEBUG_BUILD", "") == "1"
+_LIB_PATH = _build.LIB_DEBUG if _DEBUG else _build.LIB
 
 # status codes (include/qcmet.h)
 OK = 0
@@ -47,7 +50,7 @@ EXPORTS = (
     "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
     "qcmet_decode_early_stop", "qcmet_minsum_decode", "qcmet_minsum_forward",
     "qcmet_minsum_backward", "qcmet_batch_create", "qcmet_batch_run", "qcmet_batch_get_config",
-    "qcmet_batch_destroy",
+    "qcmet_batch_destroy", "qcmet_debug_checks",
 )
 
 
@@ -87,7 +90,7 @@ class DecodeOptions(ctypes.Structure):
 def _load():
     # Compile the CUDA library when it is missing or older than its sources
     # (raises without nvcc: there is no CPU fallback).
-    _build.build()
+    _build.build(debug=_DEBUG)
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"{_LIB_PATH} was not built; there is no CPU fallback")
     lib = ctypes.CDLL(_LIB_PATH)
@@ -119,6 +122,7 @@ def _load():
     lib.qcmet_status_string.argtypes = [ctypes.c_int]
     lib.qcmet_status_string.restype = ctypes.c_char_p
     lib.qcmet_version.argtypes = []
+    lib.qcmet_debug_checks.argtypes = [vp]
     for name in EXPORTS:
         if name not in ("qcmet_code_destroy", "qcmet_last_error", "qcmet_status_string",
                         "qcmet_batch_destroy"):
@@ -137,6 +141,14 @@ def _check(status: int):
 
 def library_path() -> str:
     return _LIB_PATH
+
+
+def debug_checks() -> int:
+    """Index-check bits recorded by the debug build since the last call (waits
+    for the device; raises QcmetError(UNSUPPORTED) in the release build)."""
+    bits = ctypes.c_uint32(0)
+    _check(lib.qcmet_debug_checks(ctypes.byref(bits)))
+    return int(bits.value)
 
 
 

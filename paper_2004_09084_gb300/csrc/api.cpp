@@ -10,6 +10,7 @@
 #include <string>
 
 #include "qcmet_internal.h"
+#include "trace.h"
 
 namespace {
 
@@ -202,6 +203,9 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     a.core_cols = c.core_cols;
     a.msg_slots = c.msg_slots;
     a.stage_ops = stage_ops;
+    qcmet::TraceRange range("qcmet decode: grouped kernel, %d frames, %d layer groups x %d iterations, "
+                            "%d clusters of %d", K, (int)c.layer_first.size() - 1, T, L.groups,
+                            L.cluster);
     st = qcmet::launch_decode_group(a, fmt, L, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
@@ -288,6 +292,9 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     rule.w_scale = w_scale;
     rule.w_offset = w_offset;
     std::string err;
+    qcmet::TraceRange range("qcmet decode: frame kernel, %d frames, %d layer groups x %d iterations%s",
+                            K, (int)c.layer_first.size() - 1, T,
+                            w_scale ? ", min-sum rule" : (check_every ? ", early stop" : ""));
     st = qcmet::launch_decode(a, fmt, threads, stream, err, window, hit, rule);
     if (st) return fail(st, err);
     return QCMET_OK;
@@ -427,6 +434,7 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
     float *d_post = llr_post ? reinterpret_cast<float *>(base + b_ch + b_syn + b_hard) : nullptr;
     uint8_t *d_ok = reinterpret_cast<uint8_t *>(base + b_ch + b_syn + b_hard + b_post);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    qcmet::TraceRange range("qcmet decode_host: %d frames", K);
     cudaError_t e = cudaMemcpyAsync(d_ch, llr_ch, (size_t)K * n * sizeof(float),
                                     cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail("cudaMemcpyAsync(llr_ch)", e);
@@ -593,6 +601,7 @@ int qcmet_minsum_forward(const qcmet_code *code, const float *llr_ch, const uint
     a.w_offset = w_offset;
     a.loss = loss;
     std::string err;
+    qcmet::TraceRange range("qcmet min-sum forward: %d frames x %d iterations", K, iterations);
     st = qcmet::launch_learned_forward(a, stream, err);
     if (st) return fail(st, err);
     c.learned_last = a;
@@ -618,9 +627,32 @@ int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offse
     a.g_scale = g_scale;
     a.g_offset = g_offset;
     std::string err;
+    qcmet::TraceRange range("qcmet min-sum backward: %d frames x %d iterations", a.K, a.T);
     int st = qcmet::launch_learned_backward(a, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
+}
+
+int qcmet_debug_checks(uint32_t *violations) {
+    if (!violations) return fail(QCMET_ERR_INVALID_ARG, "violations must not be NULL");
+    *violations = 0;
+#ifndef QCMET_DEBUG_CHECKS
+#define QCMET_DEBUG_CHECKS 0
+#endif
+#if QCMET_DEBUG_CHECKS
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail("cudaDeviceSynchronize", e);
+    uint32_t a = 0, b = 0;
+    std::string err;
+    int st = qcmet::take_violations_frame(&a, err);
+    if (!st) st = qcmet::take_violations_group(&b, err);
+    if (st) return fail(st, err);
+    *violations = a | b;
+    return QCMET_OK;
+#else
+    return fail(QCMET_ERR_UNSUPPORTED, "this library was built without index checks "
+                                       "(build libqcmet_debug.so for them)");
+#endif
 }
 
 const char *qcmet_last_error(void) { return g_last_error.c_str(); }

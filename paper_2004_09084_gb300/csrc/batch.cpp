@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "qcmet_internal.h"
+#include "trace.h"
 
 struct qcmet_batch {
     std::vector<qcmet_frame> frames;
@@ -416,6 +417,7 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
 
 int qcmet_batch_run(qcmet_batch *batch, void *stream) {
     if (!batch || !batch->exec) return qcmet::set_error(QCMET_ERR_INVALID_ARG, "batch must not be NULL");
+    qcmet::TraceRange range("qcmet batch: %d frames x %d iterations", batch->K, batch->T);
     cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_err("cudaGraphLaunch", e);
     return QCMET_OK;

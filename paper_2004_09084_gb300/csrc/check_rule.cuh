@@ -77,7 +77,7 @@ struct Msg<__nv_bfloat16> {
 
 struct Sched {
     const int32_t *w;
-    int32_t n_rows, n_layers, nb, Z, mb, n_zero_rows;
+    int32_t n_rows, n_layers, nb, Z, mb, n_zero_rows, core_cols, msg_slots;
     const int32_t *layer_first;
     const int4 *rows;     // DevRow
     const int4 *entries;  // DevEntry
@@ -95,6 +95,8 @@ __device__ __forceinline__ Sched make_sched(const int32_t *w) {
     s.Z = w[kHdrZ];
     s.mb = w[kHdrMb];
     s.n_zero_rows = w[kHdrZeroRows];
+    s.core_cols = w[kHdrCoreCols];
+    s.msg_slots = w[kHdrMsgSlots];
     s.layer_first = w + w[kHdrOffLayerFirst];
     s.rows = reinterpret_cast<const int4 *>(w + w[kHdrOffRows]);
     s.entries = reinterpret_cast<const int4 *>(w + w[kHdrOffEntries]);
@@ -102,6 +104,53 @@ __device__ __forceinline__ Sched make_sched(const int32_t *w) {
     s.zero_rows = w + w[kHdrOffZeroRows];
     s.col_core = w + w[kHdrOffColCore];
     return s;
+}
+
+// ---- index checks of the debug build ------------------------------------------
+//
+// Built with QCMET_DEBUG_CHECKS=1 (paper_2004_09084_gb300.build.build(debug=True),
+// libqcmet_debug.so), the kernels test every index they gather or scatter
+// against its array's extent and skip an access that would leave it,
+// recording the kind of index in a device word of the translation unit that
+// qcmet_debug_checks() reads and clears.  In the release build in_range() is
+// the constant true and the tests compile away.
+#ifndef QCMET_DEBUG_CHECKS
+#define QCMET_DEBUG_CHECKS 0
+#endif
+enum : uint32_t {
+    kBadVariable = 1u,  // a posterior / channel index outside its array
+    kBadSlot = 2u,      // a message slot or check index outside the message array
+    kBadCheck = 4u,     // a syndrome index outside the frame's checks
+};
+#if QCMET_DEBUG_CHECKS
+static __device__ uint32_t g_qcmet_violations;
+#endif
+
+__device__ __forceinline__ bool in_range(long long idx, long long extent, uint32_t kind) {
+#if QCMET_DEBUG_CHECKS
+    const bool ok = idx >= 0 && idx < extent;
+    if (!ok) atomicOr(&g_qcmet_violations, kind);
+    return ok;
+#else
+    (void)idx;
+    (void)extent;
+    (void)kind;
+    return true;
+#endif
+}
+
+// Extents the checks test against, in elements of the frame's (or group's)
+// arrays: core posteriors, channel / all variables, message slots x Z, checks.
+struct Bounds {
+    long long core, vars, msgs, checks;
+};
+__device__ __forceinline__ Bounds bounds_of(const Sched &s) {
+    Bounds b;
+    b.core = (long long)s.core_cols * s.Z;
+    b.vars = (long long)s.nb * s.Z;
+    b.msgs = (long long)s.msg_slots * s.Z;
+    b.checks = (long long)s.mb * s.Z;
+    return b;
 }
 
 // ---- one check node ----------------------------------------------------------

@@ -90,6 +90,7 @@ struct Frame {
     float *post;         // [n] output posteriors (degree-1 columns written in place)
     float *post_core;    // [core_cols][Z] posteriors of the core columns
     M *msg;              // [slots][stride]
+    Bounds bd;           // extents for the debug build's index checks
 };
 
 // Gather the V2C message q = L_qn - L_rmn(old) of edge `en` at check i.
@@ -99,9 +100,12 @@ __device__ __forceinline__ float gather_q(const int4 &en, int i, const Frame<M> 
     int j = i + en.y;
     j = j >= Z ? j - Z : j;
     const int v = en.x + j;
-    if (en.z < 0) return __ldcs(fr.ch + v);  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
-    const float lv = fr.post_core[v];
-    const float ro = first ? 0.0f : Msg<M>::load(fr.msg + (size_t)en.z * stride + i);
+    if (en.z < 0)  // degree-1 variable: L_qn - L_rmn(old) = channel LLR
+        return in_range(v, fr.bd.vars, kBadVariable) ? __ldcs(fr.ch + v) : 0.0f;
+    const float lv = in_range(v, fr.bd.core, kBadVariable) ? fr.post_core[v] : 0.0f;
+    const float ro = (first || !in_range((long long)en.z * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                         ? 0.0f
+                         : Msg<M>::load(fr.msg + (size_t)en.z * stride + i);
     return lv - ro;
 }
 
@@ -120,9 +124,10 @@ __device__ __forceinline__ void scatter_r(const int4 &en, int i, float q, float 
     const int v = en.x + j;
     if (en.z >= 0) {
         rn = Msg<M>::quantize(rn);
-        Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
-        fr.post_core[v] = q + rn;
-    } else {
+        if (in_range((long long)en.z * (long long)stride + i, fr.bd.msgs, kBadSlot))
+            Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
+        if (in_range(v, fr.bd.core, kBadVariable)) fr.post_core[v] = q + rn;
+    } else if (in_range(v, fr.bd.vars, kBadVariable)) {
         fr.post[v] = q + rn;
     }
 }
@@ -158,13 +163,18 @@ __device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int 
     const int step = blockDim.x;
     const float *src[D];
     int sh[D];
+    int xo[D], zo[DC > 0 ? DC : 1];  // variable and slot offsets (index checks of the debug build)
     M *slot[NC];
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
         sh[e] = en.y;
-        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+        xo[e] = en.x;
+        if (e < DC) {
+            slot[e] = fr.msg + (size_t)en.z * stride;
+            zo[e] = en.z;
+        }
     }
     for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
         float lv[U][D], ro[U][NC];
@@ -172,15 +182,22 @@ __device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int 
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int i = min(i0 + k * step, Z - 1);
-            par[k] = fr.syn[check_base + i] & 1u;
+            par[k] = in_range((long long)check_base + i, fr.bd.checks, kBadCheck)
+                         ? (fr.syn[check_base + i] & 1u)
+                         : 0u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                lv[k][e] = src[e][j];
+                lv[k][e] = in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable)
+                                ? src[e][j]
+                                : 0.0f;
             }
 #pragma unroll
-            for (int e = 0; e < DC; ++e) ro[k][e] = first ? 0.0f : Msg<M>::load(slot[e] + i);
+            for (int e = 0; e < DC; ++e)
+                ro[k][e] = (first || !in_range((long long)zo[e] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                               ? 0.0f
+                               : Msg<M>::load(slot[e] + i);
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -204,10 +221,13 @@ __device__ __forceinline__ void run_row_split(const int4 *__restrict__ ent, int 
                 j = j >= Z ? j - Z : j;
                 if (e < DC) {
                     rn = Msg<M>::quantize(rn);
-                    Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
-                    const_cast<float *>(src[e])[j] = q[e] + rn;
+                    if (in_range((long long)zo[e < DC ? e : 0] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                        Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
+                    if (in_range((long long)xo[e] + j, fr.bd.core, kBadVariable))
+                        const_cast<float *>(src[e])[j] = q[e] + rn;
                 } else {
-                    fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+                    if (in_range((long long)xo[e] + j, fr.bd.vars, kBadVariable))
+                        fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
                 }
             });
         }
@@ -268,13 +288,18 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
     float *stage = reinterpret_cast<float *>(qcmet_dyn_smem);
     const float *src[D];
     int sh[D];
+    int xo[D], zo[DC > 0 ? DC : 1];  // variable and slot offsets (index checks of the debug build)
     float *slot[NC];
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
         sh[e] = en.y;
-        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+        xo[e] = en.x;
+        if (e < DC) {
+            slot[e] = fr.msg + (size_t)en.z * stride;
+            zo[e] = en.z;
+        }
     }
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stage + tid);
     // copy the operands of check i into round buffer b (or nothing past Z); one group per round
@@ -285,11 +310,14 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                cp_async4(sb + e * kOp, src[e] + j);
+                if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
+                    cp_async4(sb + e * kOp, src[e] + j);
             }
             if (!first) {
 #pragma unroll
-                for (int e = 0; e < DC; ++e) cp_async4(sb + (D + e) * kOp, slot[e] + i);
+                for (int e = 0; e < DC; ++e)
+                    if (in_range((long long)zo[e] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                        cp_async4(sb + (D + e) * kOp, slot[e] + i);
             }
         }
         cp_async_commit();
@@ -298,7 +326,9 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
 #pragma unroll
     for (int r = 0; r < S - 1; ++r) {
         const int i = tid + r * step;
-        sy[r] = i < Z ? fr.syn[check_base + i] : 0u;
+        sy[r] = (i < Z && in_range((long long)check_base + i, fr.bd.checks, kBadCheck))
+                    ? fr.syn[check_base + i]
+                    : 0u;
         issue(i, r);
     }
     int buf = 0;
@@ -307,7 +337,9 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
             const int nx = i + (S - 1) * step;
             int nb = buf + (S - 1);
             nb = nb >= S ? nb - S : nb;
-            sy[S - 1] = nx < Z ? fr.syn[check_base + nx] : 0u;
+            sy[S - 1] = (nx < Z && in_range((long long)check_base + nx, fr.bd.checks, kBadCheck))
+                            ? fr.syn[check_base + nx]
+                            : 0u;
             issue(nx, nb);
         }
         cp_async_wait<S - 1>();
@@ -330,10 +362,13 @@ __device__ __forceinline__ void run_row_split_async(const int4 *__restrict__ ent
             int j = i + sh[e];
             j = j >= Z ? j - Z : j;
             if (e < DC) {
-                slot[e < DC ? e : 0][i] = rn;
-                const_cast<float *>(src[e])[j] = q[e] + rn;
+                if (in_range((long long)zo[e < DC ? e : 0] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                    slot[e < DC ? e : 0][i] = rn;
+                if (in_range((long long)xo[e] + j, fr.bd.core, kBadVariable))
+                    const_cast<float *>(src[e])[j] = q[e] + rn;
             } else {
-                fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+                if (in_range((long long)xo[e] + j, fr.bd.vars, kBadVariable))
+                    fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
             }
         });
 #pragma unroll
@@ -374,13 +409,18 @@ __device__ __forceinline__ void run_row_split_async2(const int4 *__restrict__ en
     float2 *stage = reinterpret_cast<float2 *>(qcmet_dyn_smem);
     const float *src[D];
     int sh[D];
+    int xo[D], zo[DC > 0 ? DC : 1];  // variable and slot offsets (index checks of the debug build)
     float *slot[NC];
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
         sh[e] = en.y;
-        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+        xo[e] = en.x;
+        if (e < DC) {
+            slot[e] = fr.msg + (size_t)en.z * stride;
+            zo[e] = en.z;
+        }
     }
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(stage + tid);
     auto issue = [&](int i, int b) {
@@ -390,28 +430,37 @@ __device__ __forceinline__ void run_row_split_async2(const int4 *__restrict__ en
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
+                const long long ext = e < DC ? fr.bd.core : fr.bd.vars;
                 if (sh[e] & 1) {
                     const int j1 = j + 1 == Z ? 0 : j + 1;
-                    cp_async4(sb + e * kOp, src[e] + j);
-                    cp_async4(sb + e * kOp + 4, src[e] + j1);
-                } else {
+                    if (in_range((long long)xo[e] + j, ext, kBadVariable))
+                        cp_async4(sb + e * kOp, src[e] + j);
+                    if (in_range((long long)xo[e] + j1, ext, kBadVariable))
+                        cp_async4(sb + e * kOp + 4, src[e] + j1);
+                } else if (in_range((long long)xo[e] + j + 1, ext, kBadVariable)) {
                     cp_async8(sb + e * kOp, src[e] + j);
                 }
             }
             if (!first) {
 #pragma unroll
-                for (int e = 0; e < DC; ++e) cp_async8(sb + (D + e) * kOp, slot[e] + i);
+                for (int e = 0; e < DC; ++e)
+                    if (in_range((long long)zo[e] * (long long)stride + i + 1, fr.bd.msgs, kBadSlot))
+                        cp_async8(sb + (D + e) * kOp, slot[e] + i);
             }
         }
         cp_async_commit();
     };
-    unsigned sy = reinterpret_cast<const uint16_t *>(fr.syn + check_base)[tid];
+    unsigned sy = in_range((long long)check_base + 2 * tid + 1, fr.bd.checks, kBadCheck)
+                      ? reinterpret_cast<const uint16_t *>(fr.syn + check_base)[tid]
+                      : 0u;
     issue(2 * tid, 0);
     int buf = 0;
     for (int i = 2 * tid; i < Z; i += step) {
         const int nx = i + step;
         const unsigned sy_next =
-            nx < Z ? reinterpret_cast<const uint16_t *>(fr.syn + check_base)[nx >> 1] : 0u;
+            (nx < Z && in_range((long long)check_base + nx + 1, fr.bd.checks, kBadCheck))
+                ? reinterpret_cast<const uint16_t *>(fr.syn + check_base)[nx >> 1]
+                : 0u;
         issue(nx, buf ^ 1);
         cp_async_wait<1>();
         const float2 *sv = stage + tid + buf * (kRound / 8);
@@ -462,11 +511,14 @@ __device__ __forceinline__ void run_row_split_async2(const int4 *__restrict__ en
             float *dst = e < DC ? const_cast<float *>(src[e]) : fr.post + (src[e] - fr.ch);
             const float v0 = e < DC ? pc2[e < DC ? e : 0].x : pd[0];
             const float v1 = e < DC ? pc2[e < DC ? e : 0].y : pd[1];
-            if (e < DC) *reinterpret_cast<float2 *>(slot[e < DC ? e : 0] + i) = rn2[e < DC ? e : 0];
+            const long long ext = e < DC ? fr.bd.core : fr.bd.vars;
+            if (e < DC && in_range((long long)zo[e < DC ? e : 0] * (long long)stride + i + 1, fr.bd.msgs, kBadSlot))
+                *reinterpret_cast<float2 *>(slot[e < DC ? e : 0] + i) = rn2[e < DC ? e : 0];
             if (sh[e] & 1) {
-                dst[j] = v0;
-                dst[j + 1 == Z ? 0 : j + 1] = v1;
-            } else {
+                const int j1 = j + 1 == Z ? 0 : j + 1;
+                if (in_range((long long)xo[e] + j, ext, kBadVariable)) dst[j] = v0;
+                if (in_range((long long)xo[e] + j1, ext, kBadVariable)) dst[j1] = v1;
+            } else if (in_range((long long)xo[e] + j + 1, ext, kBadVariable)) {
                 *reinterpret_cast<float2 *>(dst + j) = make_float2(v0, v1);
             }
         }
@@ -504,7 +556,9 @@ __device__ __forceinline__ void run_row_pair(const int4 *__restrict__ ent, int c
 #pragma unroll
         for (int k = 0; k < UP; ++k) {
             const int ic = min(i0 + k * 16 + (lane & 15), Z - 1);
-            par[k] = part == 0 ? (fr.syn[check_base + ic] & 1u) : 0u;
+            par[k] = (part == 0 && in_range((long long)check_base + ic, fr.bd.checks, kBadCheck))
+                         ? (fr.syn[check_base + ic] & 1u)
+                         : 0u;
 #pragma unroll
             for (int el = 0; el < E && kBatch; ++el) {
                 const int e = min(part * E + el, D - 1);
@@ -512,8 +566,11 @@ __device__ __forceinline__ void run_row_pair(const int4 *__restrict__ ent, int c
                 int j = ic + en.y;
                 j = j >= Z ? j - Z : j;
                 const float *src = en.z < 0 ? fr.ch : fr.post_core;
-                lv[k][el] = src[en.x + j];
-                const bool has_old = !first && en.z >= 0;
+                lv[k][el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
+                                ? src[en.x + j]
+                                : 0.0f;
+                const bool has_old = !first && en.z >= 0 &&
+                                     in_range((long long)en.z * (long long)stride + ic, fr.bd.msgs, kBadSlot);
                 ro[k][el] = has_old ? Msg<M>::load(fr.msg + (size_t)en.z * stride + ic) : 0.0f;
             }
         }
@@ -665,9 +722,10 @@ __device__ __forceinline__ void scatter_minsum(const int4 &en, int i, float q, f
     const int v = en.x + j;
     if (!deg1) {
         rn = Msg<M>::quantize(rn);
-        Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
-        fr.post_core[v] = q + rn;
-    } else {
+        if (in_range((long long)en.z * (long long)stride + i, fr.bd.msgs, kBadSlot))
+            Msg<M>::store(fr.msg + (size_t)en.z * stride + i, rn);
+        if (in_range(v, fr.bd.core, kBadVariable)) fr.post_core[v] = q + rn;
+    } else if (in_range(v, fr.bd.vars, kBadVariable)) {
         fr.post[v] = q + rn;
     }
 }
@@ -683,13 +741,18 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
     const int step = blockDim.x;
     const float *src[D];
     int sh[D];
+    int xo[D], zo[DC > 0 ? DC : 1];  // variable and slot offsets (index checks of the debug build)
     M *slot[NC];
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.post_core : fr.ch) + en.x;
         sh[e] = en.y;
-        if (e < DC) slot[e] = fr.msg + (size_t)en.z * stride;
+        xo[e] = en.x;
+        if (e < DC) {
+            slot[e] = fr.msg + (size_t)en.z * stride;
+            zo[e] = en.z;
+        }
     }
     for (int i0 = threadIdx.x; i0 < Z; i0 += step * U) {
         float lv[U][D], ro[U][NC];
@@ -697,15 +760,22 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int i = min(i0 + k * step, Z - 1);
-            par[k] = fr.syn[check_base + i] & 1u;
+            par[k] = in_range((long long)check_base + i, fr.bd.checks, kBadCheck)
+                         ? (fr.syn[check_base + i] & 1u)
+                         : 0u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                lv[k][e] = src[e][j];
+                lv[k][e] = in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable)
+                                ? src[e][j]
+                                : 0.0f;
             }
 #pragma unroll
-            for (int e = 0; e < DC; ++e) ro[k][e] = first ? 0.0f : Msg<M>::load(slot[e] + i);
+            for (int e = 0; e < DC; ++e)
+                ro[k][e] = (first || !in_range((long long)zo[e] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                               ? 0.0f
+                               : Msg<M>::load(slot[e] + i);
         }
 #pragma unroll
         for (int k = 0; k < U; ++k) {
@@ -740,10 +810,13 @@ __device__ __forceinline__ void run_row_minsum(const int4 *__restrict__ ent, int
                 j = j >= Z ? j - Z : j;
                 if (e < DC) {
                     rn = Msg<M>::quantize(rn);
-                    Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
-                    const_cast<float *>(src[e])[j] = q[e] + rn;
+                    if (in_range((long long)zo[e < DC ? e : 0] * (long long)stride + i, fr.bd.msgs, kBadSlot))
+                        Msg<M>::store(slot[e < DC ? e : 0] + i, rn);
+                    if (in_range((long long)xo[e] + j, fr.bd.core, kBadVariable))
+                        const_cast<float *>(src[e])[j] = q[e] + rn;
                 } else {
-                    fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
+                    if (in_range((long long)xo[e] + j, fr.bd.vars, kBadVariable))
+                        fr.post[(src[e] - fr.ch) + j] = q[e] + rn;
                 }
             }
         }
@@ -767,7 +840,9 @@ __device__ __forceinline__ void run_row_pair_minsum(const int4 *__restrict__ ent
         const bool valid = i < Z;
         const int ic = min(i, Z - 1);
         float q[E];
-        unsigned par = part == 0 ? (fr.syn[check_base + ic] & 1u) : 0u;
+        unsigned par = (part == 0 && in_range((long long)check_base + ic, fr.bd.checks, kBadCheck))
+                           ? (fr.syn[check_base + ic] & 1u)
+                           : 0u;
         // all of this lane's loads first (source selected; indices clamped), for
         // at most five edges per lane; more are gathered as used
         constexpr bool kBatch = E <= 5;
@@ -778,8 +853,13 @@ __device__ __forceinline__ void run_row_pair_minsum(const int4 *__restrict__ ent
             int j = ic + en.y;
             j = j >= Z ? j - Z : j;
             const float *src = en.z < 0 ? fr.ch : fr.post_core;
-            lv[el] = src[en.x + j];
-            ro[el] = (!first && en.z >= 0) ? Msg<M>::load(fr.msg + (size_t)en.z * stride + ic) : 0.0f;
+            lv[el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
+                         ? src[en.x + j]
+                         : 0.0f;
+            ro[el] = (!first && en.z >= 0 &&
+                      in_range((long long)en.z * (long long)stride + ic, fr.bd.msgs, kBadSlot))
+                         ? Msg<M>::load(fr.msg + (size_t)en.z * stride + ic)
+                         : 0.0f;
         }
         float m1 = INFINITY, m2 = INFINITY;
         int i1 = -1;
@@ -885,6 +965,8 @@ __device__ __noinline__ void write_outputs(const Sched &s, const DecodeArgs &a, 
         const size_t base = (size_t)c * Z;
         const float *core = kind == kColCore ? fr.post_core + (size_t)s.col_core[c] * Z : nullptr;
         for (int i = threadIdx.x; i < Z; i += blockDim.x) {
+            if (!in_range((long long)base + i, fr.bd.vars, kBadVariable)) continue;
+            if (core && !in_range((long long)s.col_core[c] * Z + i, fr.bd.core, kBadVariable)) continue;
             float L;
             if (core) {
                 L = core[i];
@@ -916,14 +998,18 @@ __device__ __forceinline__ int row_fails(const int4 *__restrict__ ent, int check
 #pragma unroll
         for (int k = 0; k < U; ++k) {
             const int i = min(i0 + k * step, Z - 1);
-            par[k] = fr.syn[check_base + i] & 1u;
+            par[k] = in_range((long long)check_base + i, fr.bd.checks, kBadCheck)
+                         ? (fr.syn[check_base + i] & 1u)
+                         : 0u;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
                 const int4 en = ent[e];
                 int j = i + en.y;
                 j = j >= Z ? j - Z : j;
                 const float *src = en.z < 0 ? fr.post : fr.post_core;
-                lv[k][e] = src[en.x + j];
+                lv[k][e] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
+                               ? src[en.x + j]
+                               : 0.0f;
             }
         }
         unsigned bad = 0u;
@@ -943,13 +1029,16 @@ template <typename M>
 __device__ __forceinline__ int row_fails_any(const int4 *__restrict__ ent, int degree,
                                              int check_base, const Frame<M> &fr, int Z) {
     for (int i = threadIdx.x; i < Z; i += blockDim.x) {
-        unsigned p = fr.syn[check_base + i] & 1u;
+        unsigned p = in_range((long long)check_base + i, fr.bd.checks, kBadCheck)
+                         ? (fr.syn[check_base + i] & 1u)
+                         : 0u;
         for (int e = 0; e < degree; ++e) {
             const int4 en = ent[e];
             int j = i + en.y;
             j = j >= Z ? j - Z : j;
             const float *src = en.z < 0 ? fr.post : fr.post_core;
-            p ^= src[en.x + j] < 0.0f ? 1u : 0u;
+            if (in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable))
+                p ^= src[en.x + j] < 0.0f ? 1u : 0u;
         }
         if (p) return 1;
     }
@@ -967,7 +1056,8 @@ __device__ __noinline__ int syndrome_fails(const Sched s, const Frame<M> fr) {
     int bad = 0;
     for (int zr = 0; zr < s.n_zero_rows; ++zr) {
         const size_t cb = (size_t)s.zero_rows[zr] * Z;
-        for (int i = threadIdx.x; i < Z; i += blockDim.x) bad |= fr.syn[cb + i] & 1;
+        for (int i = threadIdx.x; i < Z; i += blockDim.x)
+            if (in_range((long long)cb + i, fr.bd.checks, kBadCheck)) bad |= fr.syn[cb + i] & 1;
     }
     if (__syncthreads_or(bad)) return 1;
     for (int j = 0; j < s.n_rows; ++j) {
@@ -1002,13 +1092,20 @@ __device__ __forceinline__ void decode_one_frame(const Sched &s, const DecodeArg
     fr.post = a.post + (size_t)f * n;
     fr.post_core = a.post_core + (size_t)f * (size_t)a.core_cols * Z;
     fr.msg = static_cast<M *>(a.msgs) + (size_t)f * (size_t)a.msg_slots * stride;
+    fr.bd.core = (long long)a.core_cols * Z;
+    fr.bd.vars = (long long)n;
+    fr.bd.msgs = (long long)a.msg_slots * (long long)stride;
+    fr.bd.checks = (long long)a.m;
 
     // Step 1: L_qn = channel LLR for every variable that carries state.
     for (int c = 0; c < s.nb; ++c) {
         if (s.col_kind[c] != kColCore) continue;
         const float *src = fr.ch + (size_t)c * Z;
         float *dst = fr.post_core + (size_t)s.col_core[c] * Z;
-        for (int i = threadIdx.x; i < Z; i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < Z; i += blockDim.x)
+            if (in_range((long long)c * Z + i, fr.bd.vars, kBadVariable) &&
+                in_range((long long)s.col_core[c] * Z + i, fr.bd.core, kBadVariable))
+                dst[i] = src[i];
     }
     __syncthreads();
 
@@ -1125,6 +1222,28 @@ __global__ void __launch_bounds__(kDefaultThreads, 1) decode_batch_kernel(const 
         decode_one_frame<M, kRuleSumProduct, A>(s, a, 0, nullptr, nullptr);
     }
 }
+
+}  // namespace
+
+int take_violations_frame(uint32_t *bits, std::string &err) {
+    *bits = 0;
+#if QCMET_DEBUG_CHECKS
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_qcmet_violations, sizeof v);
+    const uint32_t zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_qcmet_violations, &zero, sizeof zero);
+    if (e != cudaSuccess) {
+        err = std::string("reading the index-check word: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    *bits = v;
+#else
+    (void)err;
+#endif
+    return QCMET_OK;
+}
+
+namespace {
 
 int sm_count_cached() {
     static int count[64] = {0};

@@ -300,6 +300,7 @@ struct GFrame {
     float4 *core4;                   // [core_cols][Z] posteriors of the core columns
     typename MsgVec<M>::V *msg4;     // [slots][Z] messages
     Policies pol;
+    Bounds bd;                       // extents for the debug build's index checks
 };
 
 // Rows of degree DC + D1 <= 4 (core edges first), one thread per check and
@@ -328,12 +329,17 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
     const float4 *src[D];
     int sh[D];
     V *slot[NC];
+    int xo[D], zo[NC];  // variable and slot offsets (index checks of the debug build)
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.core4 : fr.ch4) + en.x;
         sh[e] = en.y;
-        if (e < DC) slot[e] = fr.msg4 + (size_t)en.z * (size_t)Z;
+        xo[e] = en.x;
+        if (e < DC) {
+            slot[e] = fr.msg4 + (size_t)en.z * (size_t)Z;
+            zo[e] = en.z;
+        }
     }
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
     auto issue = [&](int i, int b) {
@@ -343,12 +349,14 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             for (int e = 0; e < D; ++e) {
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
-                cp_async16_cg(sb + e * opb, src[e] + j, e < DC ? fr.pol.post : fr.pol.in);
+                if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
+                    cp_async16_cg(sb + e * opb, src[e] + j, e < DC ? fr.pol.post : fr.pol.in);
             }
             if (!first) {
 #pragma unroll
                 for (int e = 0; e < DC; ++e)
-                    MV::copy_async(sb + (D + e) * opb, slot[e] + i, fr.pol.msg);
+                    if (in_range((long long)zo[e] * Z + i, fr.bd.msgs, kBadSlot))
+                        MV::copy_async(sb + (D + e) * opb, slot[e] + i, fr.pol.msg);
             }
         }
         g_commit();
@@ -357,7 +365,9 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) {
         const int i = lo + tid + k * nt;
-        sy[k] = i < hi ? ld4(fr.syn4 + check_base + i, fr.pol.in) : 0u;
+        sy[k] = (i < hi && in_range((long long)check_base + i, fr.bd.checks, kBadCheck))
+                    ? ld4(fr.syn4 + check_base + i, fr.pol.in)
+                    : 0u;
         issue(i, k);
     }
     int buf = 0;
@@ -366,7 +376,9 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             const int nx = i + (S - 1) * nt;
             int nb = buf + (S - 1);
             nb = nb >= S ? nb - S : nb;
-            sy[S - 1] = nx < hi ? ld4(fr.syn4 + check_base + nx, fr.pol.in) : 0u;
+            sy[S - 1] = (nx < hi && in_range((long long)check_base + nx, fr.bd.checks, kBadCheck))
+                            ? ld4(fr.syn4 + check_base + nx, fr.pol.in)
+                            : 0u;
             issue(nx, nb);
         }
         g_wait<S - 1>();
@@ -410,8 +422,10 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             if (e >= DC && !last) continue;
             int j = i + sh[e];
             j = j >= Z ? j - Z : j;
-            if (e < DC) MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0], fr.pol.msg);
-            st16(const_cast<float4 *>(src[e]) + j, lv[e], e < DC ? fr.pol.post : fr.pol.in);
+            if (e < DC && in_range((long long)zo[e < DC ? e : 0] * Z + i, fr.bd.msgs, kBadSlot))
+                MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0], fr.pol.msg);
+            if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
+                st16(const_cast<float4 *>(src[e]) + j, lv[e], e < DC ? fr.pol.post : fr.pol.in);
         }
 #pragma unroll
         for (int k = 0; k < S - 1; ++k) sy[k] = sy[k + 1];
@@ -438,7 +452,10 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
         const int i = i0 + (lane & 15);
         const bool valid = i < hi;
         const int ic = valid ? i : hi - 1;
-        const uint32_t par4 = part == 0 ? ld4(fr.syn4 + check_base + ic, fr.pol.in) : 0u;
+        const uint32_t par4 =
+            (part == 0 && in_range((long long)check_base + ic, fr.bd.checks, kBadCheck))
+                ? ld4(fr.syn4 + check_base + ic, fr.pol.in)
+                : 0u;
         float4 lv[E], ro[E];
 #pragma unroll
         for (int el = 0; el < E; ++el) {
@@ -446,9 +463,12 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             const int4 en = ent[e];
             int j = ic + en.y;
             j = j >= Z ? j - Z : j;
-            lv[el] = ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
-                          en.z < 0 ? fr.pol.in : fr.pol.post);
-            ro[el] = (!first && en.z >= 0)
+            lv[el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
+                         ? ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
+                                en.z < 0 ? fr.pol.in : fr.pol.post)
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            ro[el] = (!first && en.z >= 0 &&
+                      in_range((long long)en.z * Z + ic, fr.bd.msgs, kBadSlot))
                          ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic, fr.pol.msg)
                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -505,9 +525,11 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             int j = i + en.y;
             j = j >= Z ? j - Z : j;
             if (en.z >= 0) {
-                MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el], fr.pol.msg);
-                st16(fr.core4 + en.x + j, lv[el], fr.pol.post);
-            } else {
+                if (in_range((long long)en.z * Z + i, fr.bd.msgs, kBadSlot))
+                    MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el], fr.pol.msg);
+                if (in_range((long long)en.x + j, fr.bd.core, kBadVariable))
+                    st16(fr.core4 + en.x + j, lv[el], fr.pol.post);
+            } else if (in_range((long long)en.x + j, fr.bd.vars, kBadVariable)) {
                 st16(fr.ch4 + en.x + j, lv[el], fr.pol.in);
             }
         }
@@ -611,8 +633,9 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
 #pragma unroll
             for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(io.ch[f] + cb + v) : 1.0f;
             const float4 x4 = make_float4(x[0], x[1], x[2], x[3]);
-            fr.ch4[cb + v] = x4;
-            if (core) fr.core4[(size_t)cc * Z + v] = x4;
+            if (in_range((long long)cb + v, fr.bd.vars, kBadVariable)) fr.ch4[cb + v] = x4;
+            if (core && in_range((long long)cc * Z + v, fr.bd.core, kBadVariable))
+                fr.core4[(size_t)cc * Z + v] = x4;
         }
     }
     for (int l = 0; l < s.mb; ++l) {
@@ -622,7 +645,8 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
                 if (f < nf) w |= (uint32_t)(__ldcs(io.syn[f] + lb + i) & 1u) << (8 * f);
-            const_cast<uint32_t *>(fr.syn4)[lb + i] = w;
+            if (in_range((long long)lb + i, fr.bd.checks, kBadCheck))
+                const_cast<uint32_t *>(fr.syn4)[lb + i] = w;
         }
     }
     cluster_sync();
@@ -647,7 +671,11 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
         const int cc = s.col_core[c];
         const size_t cb = (size_t)c * Z;
         for (int v = lo + tid; v < hi; v += nt) {
-            const float4 L4 = core ? __ldcg(fr.core4 + (size_t)cc * Z + v) : __ldcg(fr.ch4 + cb + v);
+            const bool ok = core ? in_range((long long)cc * Z + v, fr.bd.core, kBadVariable)
+                                 : in_range((long long)cb + v, fr.bd.vars, kBadVariable);
+            const float4 L4 = !ok  ? make_float4(0.f, 0.f, 0.f, 0.f)
+                              : core ? __ldcg(fr.core4 + (size_t)cc * Z + v)
+                                     : __ldcg(fr.ch4 + cb + v);
 #pragma unroll
             for (int f = 0; f < kGF; ++f) {
                 if (f >= nf) break;
@@ -660,18 +688,20 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     uint32_t bad = 0u;
     for (int zr = 0; zr < s.n_zero_rows; ++zr) {
         const size_t lb = (size_t)s.zero_rows[zr] * Z;
-        for (int i = lo + tid; i < hi; i += nt) bad |= fr.syn4[lb + i];
+        for (int i = lo + tid; i < hi; i += nt)
+            if (in_range((long long)lb + i, fr.bd.checks, kBadCheck)) bad |= fr.syn4[lb + i];
     }
     for (int j = 0; j < s.n_rows; ++j) {
         const int4 row = s.rows[j];
         const int4 *ent = s.entries + row.x;
         for (int i = lo + tid; i < hi; i += nt) {
-            uint32_t p = fr.syn4[row.z + i];
+            uint32_t p = in_range((long long)row.z + i, fr.bd.checks, kBadCheck) ? fr.syn4[row.z + i] : 0u;
             for (int e = 0; e < row.y; ++e) {
                 const int4 en = ent[e];
                 int jj = i + en.y;
                 jj = jj >= Z ? jj - Z : jj;
-                p ^= sign_bytes(__ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + jj));
+                if (in_range((long long)en.x + jj, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable))
+                    p ^= sign_bytes(__ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + jj));
             }
             bad |= p;
         }
@@ -738,10 +768,11 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
         io.hard[f] = have ? a.hard + (size_t)(f0 + f) * n : nullptr;
         io.ok[f] = have ? a.ok + f0 + f : nullptr;
     }
-    const GFrame<M> fr = group_scratch<M>(
+    GFrame<M> fr = group_scratch<M>(
         static_cast<float4 *>(a.ch4) + (size_t)g * n, a.syn4 + (size_t)g * m,
         static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * Z,
         static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * Z);
+    fr.bd = bounds_of(s);
     decode_group_body<M, S>(s, io, fr, a.T, r, C, &s_fail);
 }
 
@@ -787,7 +818,8 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
             io.hard[f] = jb.hard[f];
             io.ok[f] = jb.ok[f];
         }
-        const GFrame<M> fr = group_scratch<M>(jb.ch4, jb.syn4, jb.core4, jb.msgs4);
+        GFrame<M> fr = group_scratch<M>(jb.ch4, jb.syn4, jb.core4, jb.msgs4);
+        fr.bd = bounds_of(s);
         decode_group_body<M, S>(s, io, fr, b.T, r, C, &s_fail);
     }
 }
@@ -913,6 +945,24 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                                : "no cluster size can be scheduled on this device";
         return QCMET_ERR_UNSUPPORTED;
     }
+    return QCMET_OK;
+}
+
+int take_violations_group(uint32_t *bits, std::string &err) {
+    *bits = 0;
+#if QCMET_DEBUG_CHECKS
+    uint32_t v = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(&v, g_qcmet_violations, sizeof v);
+    const uint32_t zero = 0;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_qcmet_violations, &zero, sizeof zero);
+    if (e != cudaSuccess) {
+        err = std::string("reading the index-check word: ") + cudaGetErrorString(e);
+        return QCMET_ERR_CUDA;
+    }
+    *bits = v;
+#else
+    (void)err;
+#endif
     return QCMET_OK;
 }
 

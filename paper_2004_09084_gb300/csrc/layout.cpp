@@ -223,6 +223,7 @@ int build_code(const int8_t *base, const int32_t *shifts, int32_t mb, int32_t nb
     pad4(w);
     w[kHdrOffColCore] = off_col_core;
     w[kHdrCoreCols] = c.core_cols;
+    w[kHdrMsgSlots] = c.msg_slots;
     w[kHdrOffLayerFirst] = im.off_layer_first;
     w[kHdrOffRows] = im.off_rows;
     w[kHdrOffEntries] = im.off_entries;

@@ -47,7 +47,7 @@ struct DevRow {
 enum : int32_t {
     kHdrRows = 0, kHdrLayers, kHdrEntries, kHdrNb, kHdrZ, kHdrMb,
     kHdrOffLayerFirst, kHdrOffRows, kHdrOffEntries, kHdrOffColKind, kHdrOffZeroRows,
-    kHdrZeroRows, kHdrOffColCore, kHdrCoreCols, kHdrPad0, kHdrPad1, kHdrWords
+    kHdrZeroRows, kHdrOffColCore, kHdrCoreCols, kHdrMsgSlots, kHdrPad1, kHdrWords
 };
 
 struct ScheduleImage {
@@ -264,6 +264,10 @@ struct GroupBatchArgs {
 int launch_decode_group_batch(const GroupBatchArgs &b, int32_t msg_format, int32_t cluster,
                               int32_t max_Z, int32_t max_image_words, void *stream,
                               std::string &err);
+
+// Debug build: read and clear the index-check words of the two kernel files.
+int take_violations_frame(uint32_t *bits, std::string &err);
+int take_violations_group(uint32_t *bits, std::string &err);
 
 // The most operands a check of a row of degree <= 4 stages (its edges'
 // posteriors or channel LLRs plus the old messages of its core edges).

@@ -132,3 +132,10 @@ def test_zero_rows_are_not_scheduled(q):
     rows, layers = code.schedule()
     assert rows.tolist() == [0, 2]
     assert layers == [[0], [2]]
+
+
+def test_release_build_has_no_index_checks(q):
+    # qcmet_debug_checks answers without touching a GPU in the release build
+    with pytest.raises(q.QcmetError) as e:
+        q.debug_checks()
+    assert e.value.status == q.ERR_UNSUPPORTED
