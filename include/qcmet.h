@@ -285,7 +285,8 @@ int qcmet_decode_noalloc(const qcmet_code *code, const float *llr_ch, const uint
  * row-major.
  *
  * qcmet_minsum_decode: decode with given weights; outputs as qcmet_decode
- *   (FP32 messages, llr_post may be NULL).
+ *   (FP32 messages, llr_post may be NULL); the grouped kernel for four frames
+ *   or more, the frame kernel otherwise (identical results).
  * qcmet_minsum_forward: training forward.  bits = device [K][n] uint8
  *   transmitted bits; loss = device [K] FP32 out, per frame the mean over
  *   iterations t and variables n of softplus(-(1 - 2 x_n) L_qn^(t)), the

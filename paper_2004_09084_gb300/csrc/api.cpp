@@ -164,12 +164,13 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
 // ceil(K/4) groups, one cluster per group.
 int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                  int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok, int32_t fmt,
-                 int32_t cluster, bool l2p, void *stream) {
+                 int32_t cluster, bool l2p, void *stream, const float *w_scale = nullptr,
+                 const float *w_offset = nullptr) {
     const int32_t stage_ops = qcmet::group_stage_ops(c);
     qcmet::GroupLaunch L;
     std::string err;
     int st = qcmet::choose_group_launch(fmt, K, c.Z, (int32_t)c.image.words.size(), stage_ops,
-                                        cluster, &L, err);
+                                        cluster, &L, err, w_scale != nullptr);
     if (st) return fail(st, err);
     const size_t G = (size_t)L.groups;
     const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
@@ -203,9 +204,11 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     a.core_cols = c.core_cols;
     a.msg_slots = c.msg_slots;
     a.stage_ops = stage_ops;
+    a.w_scale = w_scale;
+    a.w_offset = w_offset;
     qcmet::TraceRange range("qcmet decode: grouped kernel, %d frames, %d layer groups x %d iterations, "
-                            "%d clusters of %d", K, (int)c.layer_first.size() - 1, T, L.groups,
-                            L.cluster);
+                            "%d clusters of %d%s", K, (int)c.layer_first.size() - 1, T, L.groups,
+                            L.cluster, w_scale ? ", min-sum rule" : "");
     st = qcmet::launch_decode_group(a, fmt, L, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
@@ -231,14 +234,14 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
         return fail(QCMET_ERR_ALIGNMENT, "device pointers must be 16-byte aligned");
     st = ensure_device(c);
     if (st) return st;
-    const bool group_ok = check_every == 0 && !w_scale;
+    const bool group_ok = check_every == 0;
     if (kc.kernel == QCMET_KERNEL_GROUP && !group_ok)
         return fail(QCMET_ERR_UNSUPPORTED,
-                    "the grouped kernel serves the sum-product rule with fixed iterations only");
+                    "the grouped kernel serves fixed-iteration decodes only");
     if (kc.kernel == QCMET_KERNEL_GROUP || (kc.kernel == QCMET_KERNEL_AUTO && group_ok &&
                                             use_group_by_default(c, K)))
         return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc.cluster, l2p,
-                            stream);
+                            stream, w_scale, w_offset);
 
     const size_t n = (size_t)c.nb * c.Z;
     const size_t stride = qcmet::slot_stride(c.Z);

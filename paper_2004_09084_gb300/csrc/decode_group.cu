@@ -174,6 +174,20 @@ __device__ __forceinline__ float comp(const float4 &v, int f) {
     return f == 0 ? v.x : f == 1 ? v.y : f == 2 ? v.z : v.w;
 }
 
+__device__ __forceinline__ void set_comp(float4 &v, int f, float x) {
+    if (f == 0) v.x = x;
+    else if (f == 1) v.y = x;
+    else if (f == 2) v.z = x;
+    else v.w = x;
+}
+
+// Check rules: the paper's sum-product rule, or offset/scaled min-sum (the
+// learned variant) with weights wt = (scale of an edge to a core variable,
+// scale of an edge to a degree-1 variable, offset core, offset degree-1) of
+// the row and iteration.
+enum : int { kGroupSumProduct = 0, kGroupMinSum = 1 };
+constexpr float kGroupNoOtherEdge = 30.0f;  // min over the empty set (a degree-1 check)
+
 // Frames (0, 1) and (2, 3) of a float4 as packed pairs.
 __device__ __forceinline__ f2 half_of(const float4 &v, int h) {
     return h == 0 ? f2_make(v.x, v.y) : f2_make(v.z, v.w);
@@ -313,10 +327,10 @@ struct GFrame {
 // (Each row routine is its own function: it runs once per row and layer, and
 // a separate register allocation keeps the rows that a code rarely has from
 // costing the others spills.)
-template <int DC, int D1, typename M, int S>
+template <int DC, int D1, typename M, int S, int R>
 __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
                                         const GFrame<M> fr, int lo, int hi, int Z, bool first,
-                                        bool last) {
+                                        bool last, float4 wt) {
     constexpr int D = DC + D1;
     constexpr int NC = DC > 0 ? DC : 1;
     constexpr int NOP = D + DC;
@@ -389,6 +403,44 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 #pragma unroll
         for (int e = 0; e < DC; ++e)
             ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : MV::from_stage(sv + (size_t)(D + e) * nt);
+        if constexpr (R == kGroupMinSum) {
+            // min-sum, frame by frame (comparisons, no transcendentals); the
+            // operations of the frame kernel's min-sum rows
+#pragma unroll
+            for (int f = 0; f < kGF; ++f) {
+                float q[D];
+                unsigned p = (sy[0] >> (8 * f)) & 1u;
+                float m1 = INFINITY, m2 = INFINITY;
+                int i1 = -1;
+#pragma unroll
+                for (int e = 0; e < D; ++e) {
+                    q[e] = e < DC ? comp(lv[e], f) - comp(ro[e < DC ? e : 0], f) : comp(lv[e], f);
+                    p ^= q[e] < 0.0f ? 1u : 0u;
+                    const float v = fabsf(q[e]);
+                    if (v < m1) {
+                        m2 = m1;
+                        m1 = v;
+                        i1 = e;
+                    } else if (v < m2) {
+                        m2 = v;
+                    }
+                }
+#pragma unroll
+                for (int e = 0; e < D; ++e) {
+                    if (e >= DC && !last) continue;
+                    const float mn = D == 1 ? kGroupNoOtherEdge : (e == i1 ? m2 : m1);
+                    const float a_e = (e >= DC ? wt.y : wt.x) * mn - (e >= DC ? wt.w : wt.z);
+                    const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
+                    const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                    float rn = neg ? -mag : mag;
+                    if (e < DC) {
+                        rn = Msg<M>::quantize(rn);
+                        set_comp(ro[e < DC ? e : 0], f, rn);
+                    }
+                    set_comp(lv[e], f, q[e] + rn);
+                }
+            }
+        } else {
         // two frames at a time (packed); their results replace their lanes of
         // the operands (the new message in ro, the posterior q + r in lv)
 #pragma unroll
@@ -417,6 +469,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
                 set_half(lv[e], h, post);
             });
         }
+        }
 #pragma unroll
         for (int e = 0; e < D; ++e) {
             if (e >= DC && !last) continue;
@@ -438,10 +491,10 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 // parities with shuffles.  A lane loads all its edges' operands (four frames
 // each) before computing; results overwrite the operands in registers and
 // are stored as whole 16-byte words.
-template <int D, typename M>
+template <int D, typename M, int R>
 __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
                                        const GFrame<M> fr, int lo, int hi, int Z, bool first,
-                                       bool last) {
+                                       bool last, float4 wt) {
     constexpr int E = (D + 1) / 2;
     using MV = MsgVec<M>;
     const int lane = threadIdx.x & 31;
@@ -472,6 +525,56 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
                          ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic, fr.pol.msg)
                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if constexpr (R == kGroupMinSum) {
+            // min-sum, frame by frame: each lane finds the two smallest |q| of
+            // its edges and takes the partner lane's smallest by one shuffle
+            // (the frame kernel's min-sum pair rows)
+#pragma unroll
+            for (int f = 0; f < kGF; ++f) {
+                float q[E];
+                unsigned par = (par4 >> (8 * f)) & 1u;
+                float m1 = INFINITY, m2 = INFINITY;
+                int i1 = -1;
+#pragma unroll
+                for (int el = 0; el < E; ++el) {
+                    const int e = part * E + el;
+                    q[el] = 0.0f;
+                    if (valid && e < D) {
+                        q[el] = comp(lv[el], f) - comp(ro[el], f);
+                        par ^= q[el] < 0.0f ? 1u : 0u;
+                        const float v = fabsf(q[el]);
+                        if (v < m1) {
+                            m2 = m1;
+                            m1 = v;
+                            i1 = el;
+                        } else if (v < m2) {
+                            m2 = v;
+                        }
+                    }
+                }
+                const float om1 = __shfl_xor_sync(0xffffffffu, m1, 16);
+                par ^= __shfl_xor_sync(0xffffffffu, par, 16);
+                const float ex1 = fminf(m2, om1);
+                const float exo = fminf(m1, om1);
+#pragma unroll
+                for (int el = 0; el < E; ++el) {
+                    const int e = part * E + el;
+                    if (e >= D) continue;
+                    const bool deg1 = ent[e].z < 0;
+                    if (deg1 && !last) continue;
+                    const float mn = el == i1 ? ex1 : exo;
+                    const float a_e = (deg1 ? wt.y : wt.x) * mn - (deg1 ? wt.w : wt.z);
+                    const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
+                    const bool neg = ((par ^ (q[el] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                    float rn = neg ? -mag : mag;
+                    if (!deg1) {
+                        rn = Msg<M>::quantize(rn);
+                        set_comp(ro[el], f, rn);
+                    }
+                    set_comp(lv[el], f, q[el] + rn);
+                }
+            }
+        } else {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             f2 q[E], u[E];
@@ -515,6 +618,7 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
                 set_half(lv[el], h, post);
             });
         }
+        }
         if (!valid) continue;
 #pragma unroll
         for (int el = 0; el < E; ++el) {
@@ -536,17 +640,17 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
     }
 }
 
-template <typename M, int S>
+template <typename M, int S, int R>
 __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check_base,
                                           const GFrame<M> &fr, int lo, int hi, int Z, bool first,
-                                          bool last) {
+                                          bool last, float4 wt) {
     if (degree <= 4) {
         int dc = 0;
         for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
         switch (degree * 8 + dc) {
 #define QCMET_GSMALL_CASE(DD, CC)                                                            \
     case DD * 8 + CC:                                                                        \
-        grow_small<CC, DD - CC, M, S>(ent, check_base, fr, lo, hi, Z, first, last);          \
+        grow_small<CC, DD - CC, M, S, R>(ent, check_base, fr, lo, hi, Z, first, last, wt);   \
         break;
             QCMET_GSMALL_CASE(1, 0)
             QCMET_GSMALL_CASE(1, 1)
@@ -569,7 +673,7 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
     }
     switch (degree) {
 #define QCMET_GPAIR_CASE(DD) \
-    case DD: grow_pair<DD, M>(ent, check_base, fr, lo, hi, Z, first, last); break;
+    case DD: grow_pair<DD, M, R>(ent, check_base, fr, lo, hi, Z, first, last, wt); break;
         QCMET_GPAIR_CASE(5)
         QCMET_GPAIR_CASE(6)
         QCMET_GPAIR_CASE(7)
@@ -608,9 +712,12 @@ struct GroupIO {
 // barriers: one after the prologue, one per layer of every iteration and one
 // before the ok flags are written.  s_fail is a shared word of the calling
 // CTA (rank 0's collects the syndrome-test failures).
-template <typename M, int S>
+//   w_scale, w_offset: min-sum weights [T][mb][2] (R == kGroupMinSum)
+template <typename M, int S, int R>
 __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO &io, GFrame<M> fr,
-                                                  int T, int r, int C, unsigned *s_fail) {
+                                                  int T, int r, int C, unsigned *s_fail,
+                                                  const float *w_scale = nullptr,
+                                                  const float *w_offset = nullptr) {
     const int nt = blockDim.x;
     const int tid = threadIdx.x;
     const int Z = s.Z;
@@ -658,7 +765,13 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
         for (int layer = 0; layer < s.n_layers; ++layer) {
             for (int j = s.layer_first[layer]; j < s.layer_first[layer + 1]; ++j) {
                 const int4 row = s.rows[j];
-                gdispatch<M, S>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last);
+                float4 wt = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (R == kGroupMinSum) {
+                    const size_t w = ((size_t)t * s.mb + (size_t)row.w) * 2;
+                    wt = make_float4(__ldg(w_scale + w), __ldg(w_scale + w + 1), __ldg(w_offset + w),
+                                     __ldg(w_offset + w + 1));
+                }
+                gdispatch<M, S, R>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last, wt);
             }
             cluster_sync();
         }
@@ -744,7 +857,7 @@ __device__ __forceinline__ void load_image(int32_t *sw, const int32_t *image, in
 // Shared memory: the staging area, S * stage_ops * blockDim 16-byte slots
 // (stage_ops = the most operands a check of a row of degree <= 4 stages),
 // then the layer table.
-template <typename M, int S, int NT, int MINB>
+template <typename M, int S, int NT, int MINB, int R = kGroupSumProduct>
 __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
     using V = typename MsgVec<M>::V;
     const int C = (int)cluster_nctarank();
@@ -773,7 +886,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
         static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * Z,
         static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * Z);
     fr.bd = bounds_of(s);
-    decode_group_body<M, S>(s, io, fr, a.T, r, C, &s_fail);
+    decode_group_body<M, S, R>(s, io, fr, a.T, r, C, &s_fail, a.w_scale, a.w_offset);
 }
 
 // Mixed batches: persistent clusters take groups (up to four frames of one
@@ -820,14 +933,14 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
         }
         GFrame<M> fr = group_scratch<M>(jb.ch4, jb.syn4, jb.core4, jb.msgs4);
         fr.bd = bounds_of(s);
-        decode_group_body<M, S>(s, io, fr, b.T, r, C, &s_fail);
+        decode_group_body<M, S, kGroupSumProduct>(s, io, fr, b.T, r, C, &s_fail);
     }
 }
 
 // Launch variants of the kernel: (rounds staged, block bound, blocks per SM).
 struct Variant {
     int S, NT, MINB;
-    const void *kern[3];  // by message format
+    const void *kern[4];  // by message format (sum-product); [3]: min-sum, FP32 messages
 };
 
 template <int S, int NT, int MINB>
@@ -835,7 +948,9 @@ Variant make_variant() {
     return Variant{S, NT, MINB,
                    {reinterpret_cast<const void *>(&decode_group_kernel<float, S, NT, MINB>),
                     reinterpret_cast<const void *>(&decode_group_kernel<__half, S, NT, MINB>),
-                    reinterpret_cast<const void *>(&decode_group_kernel<__nv_bfloat16, S, NT, MINB>)}};
+                    reinterpret_cast<const void *>(&decode_group_kernel<__nv_bfloat16, S, NT, MINB>),
+                    reinterpret_cast<const void *>(
+                        &decode_group_kernel<float, S, NT, MINB, kGroupMinSum>)}};
 }
 
 const Variant *variants(int *count) {
@@ -871,11 +986,16 @@ size_t group_msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 16 : 8; }
 
 int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                         int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
-                        std::string &err) {
+                        std::string &err, bool minsum) {
     if (fmt != QCMET_MSG_FP32 && fmt != QCMET_MSG_FP16 && fmt != QCMET_MSG_BF16) {
         err = "unknown message format";
         return QCMET_ERR_INVALID_ARG;
     }
+    if (minsum && fmt != QCMET_MSG_FP32) {
+        err = "the min-sum rule keeps FP32 messages";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    const int kidx = minsum ? 3 : fmt;
     const int G = (K + kGF - 1) / kGF;
     int nv = 0;
     const Variant *var = variants(&nv);
@@ -892,7 +1012,7 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
     bool have = false;
     for (int vi = 0; vi < nv; ++vi) {
         if (QCMET_GROUP_VARIANT >= 0 && vi != QCMET_GROUP_VARIANT) continue;
-        const void *kern = var[vi].kern[fmt];
+        const void *kern = var[vi].kern[kidx];
         for (int k = 0; k < nc; ++k) {
             const int C = cands[k];
             const int zc = (Z + C - 1) / C;
@@ -935,6 +1055,7 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                 out->active_clusters = active;
                 out->smem = smem;
                 out->variant = vi;
+                out->kidx = kidx;
                 out->stage_ops = stage_ops;
             }
         }
@@ -1043,11 +1164,12 @@ int launch_decode_group(const GroupArgs &a, int32_t fmt, const GroupLaunch &L, v
                         std::string &err, size_t window_bytes, float hit_ratio) {
     int nv = 0;
     const Variant *var = variants(&nv);
-    if (fmt < 0 || fmt > 2 || L.variant < 0 || L.variant >= nv || a.stage_ops != L.stage_ops) {
+    if (fmt < 0 || fmt > 2 || L.variant < 0 || L.variant >= nv || a.stage_ops != L.stage_ops ||
+        L.kidx < 0 || L.kidx > 3 || (L.kidx == 3) != (a.w_scale != nullptr)) {
         err = "invalid grouped launch";
         return QCMET_ERR_INVALID_ARG;
     }
-    const void *kern = var[L.variant].kern[fmt];
+    const void *kern = var[L.variant].kern[L.kidx];
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);

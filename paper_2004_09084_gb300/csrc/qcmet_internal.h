@@ -218,6 +218,8 @@ struct GroupArgs {
     int32_t image_words;
     int32_t K, T, n, m, core_cols, msg_slots;
     int32_t stage_ops;       // most operands staged per check (rows of degree <= 4)
+    const float *w_scale;    // min-sum weights [T][mb][2], or nullptr (sum-product rule)
+    const float *w_offset;
 };
 
 // Launch shape of the grouped kernel: `groups` clusters of `cluster` CTAs.
@@ -227,6 +229,7 @@ struct GroupLaunch {
     int32_t groups = 0;
     int32_t active_clusters = 0;  // clusters of this shape the device holds at once
     int32_t variant = 0;          // kernel build (rounds staged, block bound, blocks per SM)
+    int32_t kidx = 0;             // message format, or 3 for the min-sum rule (FP32 messages)
     int32_t stage_ops = 0;
     size_t smem = 0;
 };
@@ -279,7 +282,7 @@ size_t group_msg_bytes(int32_t msg_format);
 // size for K frames of a code with expansion Z.
 int choose_group_launch(int32_t msg_format, int32_t K, int32_t Z, int32_t image_words,
                         int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
-                        std::string &err);
+                        std::string &err, bool minsum = false);
 int launch_decode_group(const GroupArgs &a, int32_t msg_format, const GroupLaunch &L,
                         void *stream, std::string &err, size_t window_bytes = 0,
                         float hit_ratio = 0.0f);

@@ -238,3 +238,20 @@ def test_training_improves_on_plain_minsum(q, learned):
         return (h != x).float().mean().item()
     trained, plain = ber(ws, wo), ber(base_s, base_o)
     assert trained < 0.8 * plain, (trained, plain)
+
+
+@pytest.mark.parametrize("Z,T", [(64, 6), (37, 4)])
+def test_grouped_minsum_equals_the_frame_kernel(q, learned, Z, T):
+    # qcmet_minsum_decode takes the grouped kernel for four frames or more and
+    # the frame kernel for fewer; the two evaluate the rule identically
+    code = synth.make_code("0.1", Z)
+    fr = synth.make_frames(code, 8, 0.2, first=900)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    ws, wo = weights(code, T, seed=5)
+    ws, wo = torch.from_numpy(ws).cuda(), torch.from_numpy(wo).cuda()
+    llr, syn = torch.from_numpy(fr.llr).cuda(), torch.from_numpy(fr.syn).cuda()
+    h, p, ok = learned.decode(qc, llr, syn, ws, wo)
+    for k in range(0, 8, 2):
+        h2, p2, ok2 = learned.decode(qc, llr[k:k + 2].contiguous(), syn[k:k + 2].contiguous(), ws, wo)
+        torch.cuda.synchronize()
+        assert torch.equal(p[k:k + 2], p2) and torch.equal(h[k:k + 2], h2) and torch.equal(ok[k:k + 2], ok2)
