@@ -327,12 +327,10 @@ struct GFrame {
 // (Each row routine is its own function: it runs once per row and layer, and
 // a separate register allocation keeps the rows that a code rarely has from
 // costing the others spills.)
-//   prefetched: grow_prefetch has already copied this row's block-private
-//   operands (old messages, degree-1 channel words) of its first S - 1 rounds
 template <int DC, int D1, typename M, int S, int R>
 __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
                                         const GFrame<M> fr, int lo, int hi, int Z, bool first,
-                                        bool last, float4 wt, bool prefetched) {
+                                        bool last, float4 wt) {
     constexpr int D = DC + D1;
     constexpr int NC = DC > 0 ? DC : 1;
     constexpr int NOP = D + DC;
@@ -358,19 +356,17 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
         }
     }
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
-    // pre: the round's block-private operands are already in flight (prefetch)
-    auto issue = [&](int i, int b, bool pre) {
+    auto issue = [&](int i, int b) {
         if (i < hi) {
             const uint32_t sb = s0 + (uint32_t)b * rb;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                if (e >= DC && pre) continue;
                 int j = i + sh[e];
                 j = j >= Z ? j - Z : j;
                 if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
                     cp_async16_cg(sb + e * opb, src[e] + j, e < DC ? fr.pol.post : fr.pol.in);
             }
-            if (!first && !pre) {
+            if (!first) {
 #pragma unroll
                 for (int e = 0; e < DC; ++e)
                     if (in_range((long long)zo[e] * Z + i, fr.bd.msgs, kBadSlot))
@@ -386,7 +382,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
         sy[k] = (i < hi && in_range((long long)check_base + i, fr.bd.checks, kBadCheck))
                     ? ld4(fr.syn4 + check_base + i, fr.pol.in)
                     : 0u;
-        issue(i, k, prefetched);
+        issue(i, k);
     }
     int buf = 0;
     for (int i = lo + tid; i < hi; i += nt) {
@@ -397,7 +393,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             sy[S - 1] = (nx < hi && in_range((long long)check_base + nx, fr.bd.checks, kBadCheck))
                             ? ld4(fr.syn4 + check_base + nx, fr.pol.in)
                             : 0u;
-            issue(nx, nb, false);
+            issue(nx, nb);
         }
         g_wait<S - 1>();
         const float4 *sv = qcmet_group_smem + tid + (size_t)buf * (rb / 16);
@@ -487,48 +483,6 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 #pragma unroll
         for (int k = 0; k < S - 1; ++k) sy[k] = sy[k + 1];
         buf = buf + 1 == S ? 0 : buf + 1;
-    }
-}
-
-// The block-private operands of the first S - 1 rounds of a row of degree
-// DC + D1 <= 4 -- old messages (written by this very thread in the previous
-// iteration) and degree-1 channel words (read only by their own check) --
-// copied into the staging slots those rounds use, before the barrier that
-// ends the previous layer; the copies join the first group the row commits.
-// The posteriors, which other blocks of the cluster may be writing, are left
-// to the row itself after the barrier.
-template <int DC, int D1, typename M, int S>
-__device__ __noinline__ void grow_prefetch(const int4 *__restrict__ ent, const GFrame<M> fr,
-                                           int lo, int hi, int Z, bool first) {
-    constexpr int D = DC + D1;
-    constexpr int NOP = D + DC;
-    using MV = MsgVec<M>;
-    const int nt = blockDim.x;
-    const int tid = threadIdx.x;
-    const uint32_t opb = (uint32_t)nt * 16u;
-    const uint32_t rb = NOP * opb;
-    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
-#pragma unroll
-    for (int k = 0; k < S - 1; ++k) {
-        const int i = lo + tid + k * nt;
-        if (i >= hi) break;
-        const uint32_t sb = s0 + (uint32_t)k * rb;
-#pragma unroll
-        for (int e = DC; e < D; ++e) {
-            const int4 en = ent[e];
-            int j = i + en.y;
-            j = j >= Z ? j - Z : j;
-            if (in_range((long long)en.x + j, fr.bd.vars, kBadVariable))
-                cp_async16_cg(sb + e * opb, fr.ch4 + en.x + j, fr.pol.in);
-        }
-        if (!first) {
-#pragma unroll
-            for (int e = 0; e < DC; ++e) {
-                const int z = ent[e].z;
-                if (in_range((long long)z * Z + i, fr.bd.msgs, kBadSlot))
-                    MV::copy_async(sb + (D + e) * opb, fr.msg4 + (size_t)z * (size_t)Z + i, fr.pol.msg);
-            }
-        }
     }
 }
 
@@ -686,48 +640,17 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
     }
 }
 
-// Rows of degree <= 4 whose block-private operands grow_prefetch can copy
-// ahead: returns 1 when it issued them.
-template <typename M, int S>
-__device__ __forceinline__ int gprefetch(int degree, const int4 *ent, const GFrame<M> &fr, int lo,
-                                         int hi, int Z, bool first) {
-    if (degree > 4) return 0;
-    int dc = 0;
-    for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
-    switch (degree * 8 + dc) {
-#define QCMET_GPRE_CASE(DD, CC) \
-    case DD * 8 + CC: grow_prefetch<CC, DD - CC, M, S>(ent, fr, lo, hi, Z, first); return 1;
-        QCMET_GPRE_CASE(1, 0)
-        QCMET_GPRE_CASE(1, 1)
-        QCMET_GPRE_CASE(2, 0)
-        QCMET_GPRE_CASE(2, 1)
-        QCMET_GPRE_CASE(2, 2)
-        QCMET_GPRE_CASE(3, 0)
-        QCMET_GPRE_CASE(3, 1)
-        QCMET_GPRE_CASE(3, 2)
-        QCMET_GPRE_CASE(3, 3)
-        QCMET_GPRE_CASE(4, 0)
-        QCMET_GPRE_CASE(4, 1)
-        QCMET_GPRE_CASE(4, 2)
-        QCMET_GPRE_CASE(4, 3)
-        QCMET_GPRE_CASE(4, 4)
-#undef QCMET_GPRE_CASE
-        default: return 0;
-    }
-}
-
 template <typename M, int S, int R>
 __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check_base,
                                           const GFrame<M> &fr, int lo, int hi, int Z, bool first,
-                                          bool last, float4 wt, bool prefetched) {
+                                          bool last, float4 wt) {
     if (degree <= 4) {
         int dc = 0;
         for (int e = 0; e < degree; ++e) dc += ent[e].z >= 0 ? 1 : 0;
         switch (degree * 8 + dc) {
 #define QCMET_GSMALL_CASE(DD, CC)                                                            \
     case DD * 8 + CC:                                                                        \
-        grow_small<CC, DD - CC, M, S, R>(ent, check_base, fr, lo, hi, Z, first, last, wt,    \
-                                         prefetched);                                        \
+        grow_small<CC, DD - CC, M, S, R>(ent, check_base, fr, lo, hi, Z, first, last, wt);   \
         break;
             QCMET_GSMALL_CASE(1, 0)
             QCMET_GSMALL_CASE(1, 1)
@@ -836,10 +759,6 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     cluster_sync();
 
     // Steps 2-3: T iterations x layers; one cluster barrier per layer.
-    // Before each layer's barrier the block copies the next layer's first row's
-    // block-private operands (grow_prefetch), so that after the barrier only
-    // the posteriors of its first rounds remain to arrive.
-    int pre = 0;  // the current layer's first row was prefetched
     for (int t = 0; t < T; ++t) {
         const bool first = t == 0;
         const bool last = t == T - 1;
@@ -852,16 +771,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
                     wt = make_float4(__ldg(w_scale + w), __ldg(w_scale + w + 1), __ldg(w_offset + w),
                                      __ldg(w_offset + w + 1));
                 }
-                gdispatch<M, S, R>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last, wt,
-                                   j == s.layer_first[layer] && pre != 0);
-            }
-            pre = 0;
-            if (layer + 1 < s.n_layers) {
-                const int4 nrow = s.rows[s.layer_first[layer + 1]];
-                pre = gprefetch<M, S>(nrow.y, s.entries + nrow.x, fr, lo, hi, Z, first);
-            } else if (t + 1 < T) {
-                const int4 nrow = s.rows[s.layer_first[0]];
-                pre = gprefetch<M, S>(nrow.y, s.entries + nrow.x, fr, lo, hi, Z, false);
+                gdispatch<M, S, R>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last, wt);
             }
             cluster_sync();
         }
