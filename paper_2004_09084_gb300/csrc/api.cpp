@@ -174,10 +174,10 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     if (st) return fail(st, err);
     const size_t G = (size_t)L.groups;
     const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
-    const size_t b_ch = round256(G * n * 16);
-    const size_t b_syn = round256(G * m * 4);
-    const size_t b_core = round256(G * (size_t)c.core_cols * c.Z * 16);
-    const size_t b_msg = round256(G * (size_t)c.msg_slots * c.Z * qcmet::group_msg_bytes(fmt));
+    if ((int64_t)c.nb * qcmet::group_zp(c.Z) > INT32_MAX)
+        return fail(QCMET_ERR_INVALID_ARG, "code too large for the grouped kernel's 32-bit offsets");
+    const qcmet::GroupScratch gs = qcmet::group_scratch_bytes(c, fmt);
+    const size_t b_ch = G * gs.ch, b_syn = G * gs.syn, b_core = G * gs.core, b_msg = G * gs.msg;
     st = grow(&c.d_group, &c.group_bytes, b_ch + b_syn + b_core + b_msg + 256,
               "cudaMalloc(grouped scratch)");
     if (st) return st;
@@ -195,6 +195,7 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     a.syn4 = reinterpret_cast<uint32_t *>(p + b_ch);
     a.core4 = p + b_ch + b_syn;
     a.msgs4 = p + b_ch + b_syn + b_core;
+    a.g_bytes = gs;
     a.image = c.d_image;
     a.image_words = (int32_t)c.image.words.size();
     a.K = K;

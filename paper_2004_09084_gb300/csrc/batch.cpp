@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <new>
@@ -108,9 +109,7 @@ int write_descriptors(qcmet_batch &b, bool alt, bool largest_first, cudaStream_t
 }
 
 size_t group_job_bytes(const qcmet::Code &c, int32_t fmt) {
-    const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
-    return r256(n * 16) + r256(m * 4) + r256((size_t)c.core_cols * c.Z * 16) +
-           r256((size_t)c.msg_slots * c.Z * qcmet::group_msg_bytes(fmt));
+    return qcmet::group_scratch_bytes(c, fmt).total();
 }
 
 // Jobs of the grouped kernel for one configuration: schedule variant and order.
@@ -141,15 +140,19 @@ int write_jobs(qcmet_batch &b, bool alt, bool largest_first, cudaStream_t s) {
             g.hard[f] = q.hard;
             g.ok[f] = q.ok;
         }
-        const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
+        if ((int64_t)c.nb * qcmet::group_zp(c.Z) > INT32_MAX) {
+            return qcmet::set_error(QCMET_ERR_INVALID_ARG,
+                                    "code too large for the grouped kernel's 32-bit offsets");
+        }
+        const qcmet::GroupScratch gs = qcmet::group_scratch_bytes(c, b.fmt);
         g.ch4 = p + off;
-        off += r256(n * 16);
+        off += gs.ch;
         g.syn4 = reinterpret_cast<uint32_t *>(p + off);
-        off += r256(m * 4);
+        off += gs.syn;
         g.core4 = p + off;
-        off += r256((size_t)c.core_cols * c.Z * 16);
+        off += gs.core;
         g.msgs4 = p + off;
-        off += r256((size_t)c.msg_slots * c.Z * qcmet::group_msg_bytes(b.fmt));
+        off += gs.msg;
         b.max_image_words = std::max(b.max_image_words, g.image_words);
     }
     std::vector<int32_t> order(J);

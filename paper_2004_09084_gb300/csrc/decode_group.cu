@@ -309,13 +309,93 @@ __device__ __forceinline__ uint32_t sign_bytes(const float4 &v) {
 // Views of one group's arrays.
 template <typename M>
 struct GFrame {
-    float4 *ch4;                     // [n]   channel (degree-1 posteriors after the last iteration)
-    const uint32_t *syn4;            // [m]   syndrome bit of frame f in byte f
-    float4 *core4;                   // [core_cols][Z] posteriors of the core columns
-    typename MsgVec<M>::V *msg4;     // [slots][Z] messages
+    float4 *ch4;                     // [nb][Zp] channel (degree-1 posteriors after the last iteration)
+    const uint32_t *syn4;            // [mb][Zp] syndrome bit of frame f in byte f
+    float4 *core4;                   // [core_cols][Zp] posteriors of the core columns
+    typename MsgVec<M>::V *msg4;     // [slots][Zp] messages
     Policies pol;
     Bounds bd;                       // extents for the debug build's index checks
+    int zp;                          // row stride of the arrays (Z rounded up to 32)
 };
+
+// The check rule on one check of a row of degree DC + D1 <= 4 (core edges
+// first) for four frames: lv holds the edges' posteriors (channel LLRs for
+// degree-1 columns), ro the old messages of the core edges (zero in the first
+// iteration), sy the syndrome bits (frame f in byte f).  The new messages
+// replace ro and the new posteriors lv (a degree-1 edge's only in the last
+// iteration).
+template <int DC, int D1, typename M, int R>
+__device__ __forceinline__ void small_rule(float4 (&lv)[DC + D1], float4 (&ro)[DC > 0 ? DC : 1],
+                                           uint32_t sy, bool last, float4 wt) {
+    constexpr int D = DC + D1;
+    if constexpr (R == kGroupMinSum) {
+        // min-sum, frame by frame (comparisons, no transcendentals); the
+        // operations of the frame kernel's min-sum rows
+#pragma unroll
+        for (int f = 0; f < kGF; ++f) {
+            float q[D];
+            unsigned p = (sy >> (8 * f)) & 1u;
+            float m1 = INFINITY, m2 = INFINITY;
+            int i1 = -1;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                q[e] = e < DC ? comp(lv[e], f) - comp(ro[e < DC ? e : 0], f) : comp(lv[e], f);
+                p ^= q[e] < 0.0f ? 1u : 0u;
+                const float v = fabsf(q[e]);
+                if (v < m1) {
+                    m2 = m1;
+                    m1 = v;
+                    i1 = e;
+                } else if (v < m2) {
+                    m2 = v;
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                if (e >= DC && !last) continue;
+                const float mn = D == 1 ? kGroupNoOtherEdge : (e == i1 ? m2 : m1);
+                const float a_e = (e >= DC ? wt.y : wt.x) * mn - (e >= DC ? wt.w : wt.z);
+                const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
+                const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
+                float rn = neg ? -mag : mag;
+                if (e < DC) {
+                    rn = Msg<M>::quantize(rn);
+                    set_comp(ro[e < DC ? e : 0], f, rn);
+                }
+                set_comp(lv[e], f, q[e] + rn);
+            }
+        }
+    } else {
+        // two frames at a time (packed); their results replace their lanes of
+        // the operands (the new message in ro, the posterior q + r in lv)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            f2 q[D], u[D];
+            unsigned p0 = (sy >> (16 * h)) & 1u;
+            unsigned p1 = (sy >> (16 * h + 8)) & 1u;
+#pragma unroll
+            for (int e = 0; e < D; ++e) {
+                const f2 l = half_of(lv[e], h);
+                q[e] = e < DC ? f2_sub(l, half_of(ro[e < DC ? e : 0], h)) : l;
+                const float q0 = f2_lo(q[e]), q1 = f2_hi(q[e]);
+                p0 ^= q0 < 0.0f ? 1u : 0u;
+                p1 ^= q1 < 0.0f ? 1u : 0u;
+                u[e] = u_of2(q0, q1);
+            }
+            exclusive_products2<D>(u, f2_splat(1.0f), f2_splat(0.0f), [&](int e, f2 a, f2 b) {
+                if (e >= DC && !last) return;
+                f2 post;
+                if (e < DC) {
+                    const f2 r = emit_pair<M, true>(a, b, q[e], p0, p1, post);
+                    set_half(ro[e < DC ? e : 0], h, r);
+                } else {
+                    emit_pair<M, false>(a, b, q[e], p0, p1, post);
+                }
+                set_half(lv[e], h, post);
+            });
+        }
+    }
+}
 
 // Rows of degree DC + D1 <= 4 (core edges first), one thread per check and
 // four frames, software-pipelined through shared memory: while a thread
@@ -351,7 +431,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
         sh[e] = en.y;
         xo[e] = en.x;
         if (e < DC) {
-            slot[e] = fr.msg4 + (size_t)en.z * (size_t)Z;
+            slot[e] = fr.msg4 + (size_t)en.z * (size_t)fr.zp;
             zo[e] = en.z;
         }
     }
@@ -369,7 +449,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             if (!first) {
 #pragma unroll
                 for (int e = 0; e < DC; ++e)
-                    if (in_range((long long)zo[e] * Z + i, fr.bd.msgs, kBadSlot))
+                    if (in_range((long long)zo[e] * fr.zp + i, fr.bd.msgs, kBadSlot))
                         MV::copy_async(sb + (D + e) * opb, slot[e] + i, fr.pol.msg);
             }
         }
@@ -403,79 +483,13 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 #pragma unroll
         for (int e = 0; e < DC; ++e)
             ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : MV::from_stage(sv + (size_t)(D + e) * nt);
-        if constexpr (R == kGroupMinSum) {
-            // min-sum, frame by frame (comparisons, no transcendentals); the
-            // operations of the frame kernel's min-sum rows
-#pragma unroll
-            for (int f = 0; f < kGF; ++f) {
-                float q[D];
-                unsigned p = (sy[0] >> (8 * f)) & 1u;
-                float m1 = INFINITY, m2 = INFINITY;
-                int i1 = -1;
-#pragma unroll
-                for (int e = 0; e < D; ++e) {
-                    q[e] = e < DC ? comp(lv[e], f) - comp(ro[e < DC ? e : 0], f) : comp(lv[e], f);
-                    p ^= q[e] < 0.0f ? 1u : 0u;
-                    const float v = fabsf(q[e]);
-                    if (v < m1) {
-                        m2 = m1;
-                        m1 = v;
-                        i1 = e;
-                    } else if (v < m2) {
-                        m2 = v;
-                    }
-                }
-#pragma unroll
-                for (int e = 0; e < D; ++e) {
-                    if (e >= DC && !last) continue;
-                    const float mn = D == 1 ? kGroupNoOtherEdge : (e == i1 ? m2 : m1);
-                    const float a_e = (e >= DC ? wt.y : wt.x) * mn - (e >= DC ? wt.w : wt.z);
-                    const float mag = fminf(fmaxf(a_e, 0.0f), kClipMax);
-                    const bool neg = ((p ^ (q[e] < 0.0f ? 1u : 0u)) & 1u) != 0u;
-                    float rn = neg ? -mag : mag;
-                    if (e < DC) {
-                        rn = Msg<M>::quantize(rn);
-                        set_comp(ro[e < DC ? e : 0], f, rn);
-                    }
-                    set_comp(lv[e], f, q[e] + rn);
-                }
-            }
-        } else {
-        // two frames at a time (packed); their results replace their lanes of
-        // the operands (the new message in ro, the posterior q + r in lv)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            f2 q[D], u[D];
-            unsigned p0 = (sy[0] >> (16 * h)) & 1u;
-            unsigned p1 = (sy[0] >> (16 * h + 8)) & 1u;
-#pragma unroll
-            for (int e = 0; e < D; ++e) {
-                const f2 l = half_of(lv[e], h);
-                q[e] = e < DC ? f2_sub(l, half_of(ro[e < DC ? e : 0], h)) : l;
-                const float q0 = f2_lo(q[e]), q1 = f2_hi(q[e]);
-                p0 ^= q0 < 0.0f ? 1u : 0u;
-                p1 ^= q1 < 0.0f ? 1u : 0u;
-                u[e] = u_of2(q0, q1);
-            }
-            exclusive_products2<D>(u, f2_splat(1.0f), f2_splat(0.0f), [&](int e, f2 a, f2 b) {
-                if (e >= DC && !last) return;
-                f2 post;
-                if (e < DC) {
-                    const f2 r = emit_pair<M, true>(a, b, q[e], p0, p1, post);
-                    set_half(ro[e < DC ? e : 0], h, r);
-                } else {
-                    emit_pair<M, false>(a, b, q[e], p0, p1, post);
-                }
-                set_half(lv[e], h, post);
-            });
-        }
-        }
+        small_rule<DC, D1, M, R>(lv, ro, sy[0], last, wt);
 #pragma unroll
         for (int e = 0; e < D; ++e) {
             if (e >= DC && !last) continue;
             int j = i + sh[e];
             j = j >= Z ? j - Z : j;
-            if (e < DC && in_range((long long)zo[e < DC ? e : 0] * Z + i, fr.bd.msgs, kBadSlot))
+            if (e < DC && in_range((long long)zo[e < DC ? e : 0] * fr.zp + i, fr.bd.msgs, kBadSlot))
                 MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0], fr.pol.msg);
             if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
                 st16(const_cast<float4 *>(src[e]) + j, lv[e], e < DC ? fr.pol.post : fr.pol.in);
@@ -521,8 +535,8 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
                                 en.z < 0 ? fr.pol.in : fr.pol.post)
                          : make_float4(0.f, 0.f, 0.f, 0.f);
             ro[el] = (!first && en.z >= 0 &&
-                      in_range((long long)en.z * Z + ic, fr.bd.msgs, kBadSlot))
-                         ? MV::load(fr.msg4 + (size_t)en.z * (size_t)Z + ic, fr.pol.msg)
+                      in_range((long long)en.z * fr.zp + ic, fr.bd.msgs, kBadSlot))
+                         ? MV::load(fr.msg4 + (size_t)en.z * (size_t)fr.zp + ic, fr.pol.msg)
                          : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if constexpr (R == kGroupMinSum) {
@@ -629,8 +643,8 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             int j = i + en.y;
             j = j >= Z ? j - Z : j;
             if (en.z >= 0) {
-                if (in_range((long long)en.z * Z + i, fr.bd.msgs, kBadSlot))
-                    MV::store(fr.msg4 + (size_t)en.z * (size_t)Z + i, ro[el], fr.pol.msg);
+                if (in_range((long long)en.z * fr.zp + i, fr.bd.msgs, kBadSlot))
+                    MV::store(fr.msg4 + (size_t)en.z * (size_t)fr.zp + i, ro[el], fr.pol.msg);
                 if (in_range((long long)en.x + j, fr.bd.core, kBadVariable))
                     st16(fr.core4 + en.x + j, lv[el], fr.pol.post);
             } else if (in_range((long long)en.x + j, fr.bd.vars, kBadVariable)) {
@@ -702,9 +716,6 @@ struct GroupIO {
     int nf;
 };
 
-#ifndef QCMET_GROUP_ALIGN
-#define QCMET_GROUP_ALIGN 1
-#endif
 
 // One cluster decodes one group (steps 1-4) with the schedule `s` in shared
 // memory; CTA r of the cluster's C owns checks [lo, hi) of every row.  Every
@@ -721,8 +732,10 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     const int nt = blockDim.x;
     const int tid = threadIdx.x;
     const int Z = s.Z;
-    // checks per CTA, a multiple of QCMET_GROUP_ALIGN
-    const int Zc = ((Z + C - 1) / C + QCMET_GROUP_ALIGN - 1) / QCMET_GROUP_ALIGN * QCMET_GROUP_ALIGN;
+    const size_t zp = (size_t)fr.zp;
+    // checks per CTA, a multiple of 32: every warp's 32 checks then start on
+    // a 128-byte line of the message and syndrome rows
+    const int Zc = ((Z + C - 1) / C + 31) / 32 * 32;
     const int lo = min(Z, r * Zc);
     const int hi = min(Z, lo + Zc);
     const int nf = io.nf;
@@ -734,26 +747,28 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     for (int c = 0; c < s.nb; ++c) {
         const bool core = s.col_kind[c] == kColCore;
         const int cc = s.col_core[c];
-        const size_t cb = (size_t)c * Z;
+        const size_t cb = (size_t)c * Z;  // caller's frame-major arrays
+        const size_t gb = (size_t)c * zp;
         for (int v = lo + tid; v < hi; v += nt) {
             float x[kGF];
 #pragma unroll
             for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(io.ch[f] + cb + v) : 1.0f;
             const float4 x4 = make_float4(x[0], x[1], x[2], x[3]);
-            if (in_range((long long)cb + v, fr.bd.vars, kBadVariable)) fr.ch4[cb + v] = x4;
-            if (core && in_range((long long)cc * Z + v, fr.bd.core, kBadVariable))
-                fr.core4[(size_t)cc * Z + v] = x4;
+            if (in_range((long long)gb + v, fr.bd.vars, kBadVariable)) fr.ch4[gb + v] = x4;
+            if (core && in_range((long long)cc * zp + v, fr.bd.core, kBadVariable))
+                fr.core4[(size_t)cc * zp + v] = x4;
         }
     }
     for (int l = 0; l < s.mb; ++l) {
         const size_t lb = (size_t)l * Z;
+        const size_t gl = (size_t)l * zp;
         for (int i = lo + tid; i < hi; i += nt) {
             uint32_t w = 0u;
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
                 if (f < nf) w |= (uint32_t)(__ldcs(io.syn[f] + lb + i) & 1u) << (8 * f);
-            if (in_range((long long)lb + i, fr.bd.checks, kBadCheck))
-                const_cast<uint32_t *>(fr.syn4)[lb + i] = w;
+            if (in_range((long long)gl + i, fr.bd.checks, kBadCheck))
+                const_cast<uint32_t *>(fr.syn4)[gl + i] = w;
         }
     }
     cluster_sync();
@@ -783,12 +798,13 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
         const bool core = s.col_kind[c] == kColCore;
         const int cc = s.col_core[c];
         const size_t cb = (size_t)c * Z;
+        const size_t gb = (size_t)c * zp;
         for (int v = lo + tid; v < hi; v += nt) {
-            const bool ok = core ? in_range((long long)cc * Z + v, fr.bd.core, kBadVariable)
-                                 : in_range((long long)cb + v, fr.bd.vars, kBadVariable);
+            const bool ok = core ? in_range((long long)cc * zp + v, fr.bd.core, kBadVariable)
+                                 : in_range((long long)gb + v, fr.bd.vars, kBadVariable);
             const float4 L4 = !ok  ? make_float4(0.f, 0.f, 0.f, 0.f)
-                              : core ? __ldcg(fr.core4 + (size_t)cc * Z + v)
-                                     : __ldcg(fr.ch4 + cb + v);
+                              : core ? __ldcg(fr.core4 + (size_t)cc * zp + v)
+                                     : __ldcg(fr.ch4 + gb + v);
 #pragma unroll
             for (int f = 0; f < kGF; ++f) {
                 if (f >= nf) break;
@@ -800,7 +816,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     }
     uint32_t bad = 0u;
     for (int zr = 0; zr < s.n_zero_rows; ++zr) {
-        const size_t lb = (size_t)s.zero_rows[zr] * Z;
+        const size_t lb = (size_t)s.zero_rows[zr] * zp;
         for (int i = lo + tid; i < hi; i += nt)
             if (in_range((long long)lb + i, fr.bd.checks, kBadCheck)) bad |= fr.syn4[lb + i];
     }
@@ -831,9 +847,10 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
     if (r == 0 && tid < nf) io.ok[tid][0] = ((*s_fail >> (8 * tid)) & 1u) ? 0 : 1;
 }
 
+// Views of one group's scratch for the code of schedule s.
 template <typename M>
-__device__ __forceinline__ GFrame<M> group_scratch(void *ch4, uint32_t *syn4, void *core4,
-                                                   void *msgs4) {
+__device__ __forceinline__ GFrame<M> group_scratch(const Sched &s, void *ch4, uint32_t *syn4,
+                                                   void *core4, void *msgs4) {
     GFrame<M> fr;
     fr.ch4 = static_cast<float4 *>(ch4);
     fr.syn4 = syn4;
@@ -841,14 +858,38 @@ __device__ __forceinline__ GFrame<M> group_scratch(void *ch4, uint32_t *syn4, vo
     fr.msg4 = static_cast<typename MsgVec<M>::V *>(msgs4);
     fr.pol = make_policies<std::is_same<M, float>::value ? QCMET_GROUP_HINT_FP32
                                                           : QCMET_GROUP_HINT_16BIT>();
+    fr.zp = (s.Z + 31) & ~31;
+    fr.bd.core = (long long)s.core_cols * fr.zp;
+    fr.bd.vars = (long long)s.nb * fr.zp;
+    fr.bd.msgs = (long long)s.msg_slots * fr.zp;
+    fr.bd.checks = (long long)s.mb * fr.zp;
     return fr;
 }
 
-// Copy a code's layer table into shared memory (every thread of the block).
-__device__ __forceinline__ void load_image(int32_t *sw, const int32_t *image, int words) {
+// Copy a code's layer table into shared memory (every thread of the block)
+// and rewrite its offsets for the grouped scratch: an entry's variable offset
+// becomes (its index among the core columns, or its base column for a
+// degree-1 column) x Zp, a row's first check l x Zp.
+__device__ __forceinline__ void load_group_image(int32_t *sw, const int32_t *image, int words) {
     const int4 *src = reinterpret_cast<const int4 *>(image);
     int4 *dst = reinterpret_cast<int4 *>(sw);
     for (int k = threadIdx.x; k < words / 4; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    const int zp = (sw[kHdrZ] + 31) & ~31;
+    const int32_t *col_core = sw + sw[kHdrOffColCore];
+    int4 *ent = reinterpret_cast<int4 *>(sw + sw[kHdrOffEntries]);
+    for (int k = threadIdx.x; k < sw[kHdrEntries]; k += blockDim.x) {
+        int4 e = ent[k];
+        e.x = (e.z >= 0 ? col_core[e.w] : e.w) * zp;
+        ent[k] = e;
+    }
+    int4 *rows = reinterpret_cast<int4 *>(sw + sw[kHdrOffRows]);
+    for (int k = threadIdx.x; k < sw[kHdrRows]; k += blockDim.x) {
+        int4 rw = rows[k];
+        rw.z = rw.w * zp;
+        rows[k] = rw;
+    }
+    __syncthreads();
 }
 
 // K frames of one code: cluster g decodes frames 4g .. 4g + 3.
@@ -859,16 +900,14 @@ __device__ __forceinline__ void load_image(int32_t *sw, const int32_t *image, in
 // then the layer table.
 template <typename M, int S, int NT, int MINB, int R = kGroupSumProduct>
 __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
-    using V = typename MsgVec<M>::V;
     const int C = (int)cluster_nctarank();
     const int r = (int)cluster_ctarank();
     const int g = (int)cluster_idx();
     __shared__ unsigned s_fail;
     int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * a.stage_ops * blockDim.x);
-    load_image(sw, a.image, a.image_words);
-    __syncthreads();
+    load_group_image(sw, a.image, a.image_words);
     const Sched s = make_sched(sw);
-    const size_t n = (size_t)a.n, m = (size_t)a.m, Z = (size_t)s.Z;
+    const size_t n = (size_t)a.n, m = (size_t)a.m;
     const int f0 = g * kGF;
     GroupIO io;
     io.nf = min(kGF, a.K - f0);
@@ -882,10 +921,10 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
         io.ok[f] = have ? a.ok + f0 + f : nullptr;
     }
     GFrame<M> fr = group_scratch<M>(
-        static_cast<float4 *>(a.ch4) + (size_t)g * n, a.syn4 + (size_t)g * m,
-        static_cast<float4 *>(a.core4) + (size_t)g * (size_t)a.core_cols * Z,
-        static_cast<V *>(a.msgs4) + (size_t)g * (size_t)a.msg_slots * Z);
-    fr.bd = bounds_of(s);
+        s, static_cast<char *>(a.ch4) + (size_t)g * a.g_bytes.ch,
+        reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(a.syn4) + (size_t)g * a.g_bytes.syn),
+        static_cast<char *>(a.core4) + (size_t)g * a.g_bytes.core,
+        static_cast<char *>(a.msgs4) + (size_t)g * a.g_bytes.msg);
     decode_group_body<M, S, R>(s, io, fr, a.T, r, C, &s_fail, a.w_scale, a.w_offset);
 }
 
@@ -916,8 +955,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
         if (k >= b.J) break;
         const GroupJob &jb = b.jobs[b.order[k]];
         if (jb.code_id != cur_code) {
-            load_image(sw, jb.image, jb.image_words);
-            __syncthreads();
+            load_group_image(sw, jb.image, jb.image_words);
             cur_code = jb.code_id;
         }
         const Sched s = make_sched(sw);
@@ -931,8 +969,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
             io.hard[f] = jb.hard[f];
             io.ok[f] = jb.ok[f];
         }
-        GFrame<M> fr = group_scratch<M>(jb.ch4, jb.syn4, jb.core4, jb.msgs4);
-        fr.bd = bounds_of(s);
+        GFrame<M> fr = group_scratch<M>(s, jb.ch4, jb.syn4, jb.core4, jb.msgs4);
         decode_group_body<M, S, kGroupSumProduct>(s, io, fr, b.T, r, C, &s_fail);
     }
 }
@@ -1099,6 +1136,17 @@ int32_t group_stage_ops(const Code &c) {
         if (d >= 1 && d <= 4) ops = d + dc > ops ? d + dc : ops;
     }
     return ops;
+}
+
+GroupScratch group_scratch_bytes(const Code &c, int32_t fmt) {
+    auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t zp = (size_t)group_zp(c.Z);
+    GroupScratch g;
+    g.ch = r256((size_t)c.nb * zp * 16);
+    g.syn = r256((size_t)c.mb * zp * 4);
+    g.core = r256((size_t)c.core_cols * zp * 16);
+    g.msg = r256((size_t)c.msg_slots * zp * group_msg_bytes(fmt));
+    return g;
 }
 
 namespace {

@@ -202,6 +202,20 @@ int launch_decode(const DecodeArgs &a, int32_t msg_format, int32_t threads, void
                   std::string &err, size_t window_bytes = 0, float hit_ratio = 0.0f,
                   const CheckRule &rule = CheckRule());
 
+// The grouped kernel's interleaved scratch for one group stores every column,
+// message slot and syndrome row with the row stride Zp = Z rounded up to 32,
+// so that each starts on a 128-byte line and the 32 checks of a warp whose
+// first check is a multiple of 32 read whole lines of messages and syndrome
+// words.
+inline int64_t group_zp(int64_t Z) { return (Z + 31) / 32 * 32; }
+
+// Bytes of one group's scratch arrays (each a multiple of 256).
+struct GroupScratch {
+    size_t ch, syn, core, msg;
+    size_t total() const { return ch + syn + core + msg; }
+};
+GroupScratch group_scratch_bytes(const Code &c, int32_t msg_format);
+
 // Arguments of the grouped decode kernel (decode_group.cu): frames 4g .. 4g+3
 // form group g and are stored interleaved, one 16-byte word per variable.
 struct GroupArgs {
@@ -210,10 +224,11 @@ struct GroupArgs {
     float *post;             // [K][n] output posteriors, or nullptr
     uint8_t *hard;           // [K][n]
     uint8_t *ok;             // [K]
-    void *ch4;               // [G][n] float4: interleaved channel (scratch)
-    uint32_t *syn4;          // [G][m]: syndrome bit of frame f in byte f (scratch)
-    void *core4;             // [G][core_cols][Z] float4: core posteriors (scratch)
-    void *msgs4;             // [G][msg_slots][Z] messages, 16 B (FP32) or 8 B (16-bit) (scratch)
+    void *ch4;               // [G][nb][Zp] float4: interleaved channel (scratch)
+    uint32_t *syn4;          // [G][mb][Zp]: syndrome bit of frame f in byte f (scratch)
+    void *core4;             // [G][core_cols][Zp] float4: core posteriors (scratch)
+    void *msgs4;             // [G][msg_slots][Zp] messages, 16 B (FP32) or 8 B (16-bit) (scratch)
+    GroupScratch g_bytes;    // bytes between consecutive groups of each array
     const int32_t *image;    // schedule image (device)
     int32_t image_words;
     int32_t K, T, n, m, core_cols, msg_slots;
@@ -247,10 +262,10 @@ struct GroupJob {
     float *post[4];          // per frame [n], or nullptr
     uint8_t *hard[4];        // per frame [n]
     uint8_t *ok[4];          // per frame [1]
-    void *ch4;               // [n] float4
-    uint32_t *syn4;          // [m]
-    void *core4;             // [core_cols][Z] float4
-    void *msgs4;             // [msg_slots][Z] messages
+    void *ch4;               // [nb][Zp] float4
+    uint32_t *syn4;          // [mb][Zp]
+    void *core4;             // [core_cols][Zp] float4
+    void *msgs4;             // [msg_slots][Zp] messages
 };
 
 struct GroupBatchArgs {
