@@ -48,6 +48,8 @@ namespace qcmet {
 namespace {
 
 constexpr int kGF = 4;                  // frames per group
+constexpr int kGroupStages = 3;         // rounds staged by the rows of degree <= 4 (every variant)
+constexpr int kPairStagedMax = 12;      // rows of degree 5 .. 12 stage their operands too
 
 extern __shared__ float4 qcmet_group_smem[];
 
@@ -502,42 +504,87 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 
 // Rows of degree 5..16: lanes l and l ^ 16 of a warp share a check, each lane
 // owning E = ceil(D/2) edges; the lanes swap their partial products and sign
-// parities with shuffles.  A lane loads all its edges' operands (four frames
-// each) before computing; results overwrite the operands in registers and
-// are stored as whole 16-byte words.
-template <int D, typename M, int R>
+// parities with shuffles.  Results overwrite the operands in registers and
+// are stored as whole 16-byte words.  STAGED: a lane copies the operands of
+// the warp's next 16 checks into its own shared-memory slots (cp.async, two
+// rounds of 2 E slots) while it computes the current ones; otherwise it loads
+// all its edges' operands, then computes.  Both give the same operands.
+template <int D, typename M, int R, bool STAGED>
 __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
                                        const GFrame<M> fr, int lo, int hi, int Z, bool first,
                                        bool last, float4 wt) {
     constexpr int E = (D + 1) / 2;
     using MV = MsgVec<M>;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const int nt = blockDim.x;
+    const int lane = tid & 31;
     const int part = lane >> 4;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
+    const int warp = tid >> 5;
+    const int nwarps = nt >> 5;
+    // staging: [2 rounds][2 E slots][nt] 16-byte words, slot el the posterior
+    // of the lane's edge el, slot E + el its old message
+    const uint32_t opb = (uint32_t)nt * 16u;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
+    auto issue = [&](int i0, int b) {
+        const int i = i0 + (lane & 15);
+        if (i0 < hi && i < hi) {
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const int e = part * E + el;
+                if (e >= D) continue;
+                const int4 en = ent[e];
+                int j = i + en.y;
+                j = j >= Z ? j - Z : j;
+                const uint32_t sb = s0 + (uint32_t)(b * 2 * E + el) * opb;
+                if (in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable))
+                    cp_async16_cg(sb, (en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
+                                  en.z < 0 ? fr.pol.in : fr.pol.post);
+                if (!first && en.z >= 0 && in_range((long long)en.z * fr.zp + i, fr.bd.msgs, kBadSlot))
+                    MV::copy_async(sb + (uint32_t)E * opb, fr.msg4 + (size_t)en.z * (size_t)fr.zp + i,
+                                   fr.pol.msg);
+            }
+        }
+        g_commit();
+    };
+    if constexpr (STAGED) issue(lo + warp * 16, 0);
+    int b = 0;
     for (int i0 = lo + warp * 16; i0 < hi; i0 += nwarps * 16) {
         const int i = i0 + (lane & 15);
         const bool valid = i < hi;
         const int ic = valid ? i : hi - 1;
+        if constexpr (STAGED) issue(i0 + nwarps * 16, b ^ 1);
         const uint32_t par4 =
             (part == 0 && in_range((long long)check_base + ic, fr.bd.checks, kBadCheck))
                 ? ld4(fr.syn4 + check_base + ic, fr.pol.in)
                 : 0u;
         float4 lv[E], ro[E];
+        if constexpr (STAGED) {
+            g_wait<1>();
+            const float4 *sv = qcmet_group_smem + tid + (size_t)b * 2 * E * nt;
 #pragma unroll
-        for (int el = 0; el < E; ++el) {
-            const int e = min(part * E + el, D - 1);
-            const int4 en = ent[e];
-            int j = ic + en.y;
-            j = j >= Z ? j - Z : j;
-            lv[el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
-                         ? ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
-                                en.z < 0 ? fr.pol.in : fr.pol.post)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
-            ro[el] = (!first && en.z >= 0 &&
-                      in_range((long long)en.z * fr.zp + ic, fr.bd.msgs, kBadSlot))
-                         ? MV::load(fr.msg4 + (size_t)en.z * (size_t)fr.zp + ic, fr.pol.msg)
-                         : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int el = 0; el < E; ++el) {
+                const int e = min(part * E + el, D - 1);
+                lv[el] = sv[(size_t)el * nt];
+                ro[el] = (!first && ent[e].z >= 0) ? MV::from_stage(sv + (size_t)(E + el) * nt)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            b ^= 1;
+        } else {
+#pragma unroll
+            for (int el = 0; el < E; ++el) {
+                const int e = min(part * E + el, D - 1);
+                const int4 en = ent[e];
+                int j = ic + en.y;
+                j = j >= Z ? j - Z : j;
+                lv[el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
+                             ? ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
+                                    en.z < 0 ? fr.pol.in : fr.pol.post)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+                ro[el] = (!first && en.z >= 0 &&
+                          in_range((long long)en.z * fr.zp + ic, fr.bd.msgs, kBadSlot))
+                             ? MV::load(fr.msg4 + (size_t)en.z * (size_t)fr.zp + ic, fr.pol.msg)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         if constexpr (R == kGroupMinSum) {
             // min-sum, frame by frame: each lane finds the two smallest |q| of
@@ -686,8 +733,12 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
         return;
     }
     switch (degree) {
-#define QCMET_GPAIR_CASE(DD) \
-    case DD: grow_pair<DD, M, R>(ent, check_base, fr, lo, hi, Z, first, last, wt); break;
+// rows of degree <= kPairStagedMax are staged (the staging area holds their
+// two rounds: group_stage_ops), higher ones load directly
+#define QCMET_GPAIR_CASE(DD)                                                                         \
+    case DD:                                                                                         \
+        grow_pair<DD, M, R, (DD <= kPairStagedMax)>(ent, check_base, fr, lo, hi, Z, first, last, wt); \
+        break;
         QCMET_GPAIR_CASE(5)
         QCMET_GPAIR_CASE(6)
         QCMET_GPAIR_CASE(7)
@@ -993,8 +1044,8 @@ Variant make_variant() {
 const Variant *variants(int *count) {
     // (four staged rounds measured no faster than three)
     static const Variant v[] = {
-        make_variant<3, 512, 1>(),
-        make_variant<3, 256, 2>(),
+        make_variant<kGroupStages, 512, 1>(),
+        make_variant<kGroupStages, 256, 2>(),
     };
     *count = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -1133,7 +1184,11 @@ int32_t group_stage_ops(const Code &c) {
             ++d;
             dc += c.col_degree[col] > 1 ? 1 : 0;
         }
-        if (d >= 1 && d <= 4) ops = d + dc > ops ? d + dc : ops;
+        int32_t need = 0;
+        if (d >= 1 && d <= 4) need = d + dc;
+        // a staged pair row: two rounds of 2 E slots, E = ceil(d / 2)
+        if (d > 4 && d <= kPairStagedMax) need = (4 * ((d + 1) / 2) + kGroupStages - 1) / kGroupStages;
+        ops = need > ops ? need : ops;
     }
     return ops;
 }
@@ -1152,7 +1207,7 @@ GroupScratch group_scratch_bytes(const Code &c, int32_t fmt) {
 namespace {
 template <typename M>
 const void *group_batch_kernel_ptr() {
-    return reinterpret_cast<const void *>(&decode_group_batch_kernel<M, 3, 512, 1>);
+    return reinterpret_cast<const void *>(&decode_group_batch_kernel<M, kGroupStages, 512, 1>);
 }
 }  // namespace
 
@@ -1169,7 +1224,7 @@ int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t clus
     if (b.J <= 0) return QCMET_OK;
     const int C = cluster;
     const int threads = group_threads((max_Z + C - 1) / C, 512);
-    const size_t smem = group_smem(3, threads, b.stage_ops, max_image_words);
+    const size_t smem = group_smem(kGroupStages, threads, b.stage_ops, max_image_words);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
