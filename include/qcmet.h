@@ -141,10 +141,12 @@ int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *laye
  *     interleaved (the four frames' values of a variable, a message or a
  *     syndrome bit form one 16-byte word), and a thread-block cluster of
  *     cluster_size blocks (0 = chosen by the library from the device's
- *     cluster occupancy; else 1, 2, 4 or 8) shares the checks of each row of
- *     one group, with one cluster barrier per layer.  Sum-product rule, fixed
- *     iterations.  Scratch: ceil(K/4) * (16 n + 4 m + 16 core_columns Z +
- *     msg_slots Z (16 for FP32, 8 for 16-bit messages)) bytes.
+ *     cluster occupancy; else 1 .. 16, sizes above 8 where the device allows
+ *     them) shares the checks of each row of one or two groups, with one
+ *     cluster barrier per layer.  Sum-product or min-sum rule, fixed
+ *     iterations.  Scratch: ceil(K/4) * (16 nb Zp + 4 mb Zp + 16 core_columns
+ *     Zp + msg_slots Zp (16 for FP32, 8 for 16-bit messages)) bytes, Zp = Z
+ *     rounded up to 32, each term rounded up to 256.
  *     The grouped kernel gives each memory access an L2 eviction priority
  *     (the streamed messages, channel and syndrome evict first, so that the
  *     core posteriors stay in L2) and ignores l2_persist.
@@ -161,8 +163,9 @@ typedef struct {
                                   of 32, <= 1024 (the grouped kernel sizes its own)  */
     int32_t l2_persist;        /* 0 = off, 1 = persisting L2 window over the state  */
     int32_t kernel;            /* QCMET_KERNEL_*                                    */
-    int32_t cluster_size;      /* grouped kernel: 0 = automatic, else 1, 2, 4 or 8  */
-    int32_t reserved[3];       /* set to 0                                          */
+    int32_t cluster_size;      /* grouped kernel: 0 = automatic, else 1 .. 16        */
+    int32_t groups_per_cluster; /* grouped kernel: 0 = automatic, else 1 or 2       */
+    int32_t reserved[2];       /* set to 0                                          */
 } qcmet_decode_options;
 /* The frame kernel's default block is 896 threads for FP32 messages (a kernel
  * built for that size, with more registers per thread) and 1024 for
@@ -364,6 +367,32 @@ int qcmet_batch_run(qcmet_batch *batch, void *stream);
 int qcmet_batch_get_config(const qcmet_batch *batch, qcmet_batch_config *out);
 /* Frees the plan (not the codes or the caller's buffers).  NULL is a no-op. */
 void qcmet_batch_destroy(qcmet_batch *batch);
+
+/*
+ * The launch shape a grouped-kernel decode of K frames of `code` with these
+ * options (NULL = defaults; msg_format and cluster_size are used) would take on
+ * the current device: clusters of cluster_size blocks, each owning
+ * groups_per_cluster groups of four frames (1 or 2; with 2 the cluster's blocks
+ * split the two groups' checks between them), threads_per_block threads and
+ * shared_bytes of dynamic shared memory per block; `clusters` clusters, `blocks`
+ * blocks in all, of which the device holds active_clusters clusters at once.
+ * The library chooses the shape to minimise the checks each SM owns per row
+ * (times the waves of clusters); the choice changes no result.  Nothing runs
+ * on the device.  Errors: INVALID_ARG, UNSUPPORTED (no shape schedulable),
+ * CUDA.
+ */
+typedef struct {
+    int32_t cluster_size;
+    int32_t groups_per_cluster;
+    int32_t threads_per_block;
+    int32_t clusters;
+    int32_t blocks;
+    int32_t active_clusters;
+    int32_t shared_bytes;
+    int32_t reserved;
+} qcmet_group_plan_t;
+int qcmet_group_plan(const qcmet_code *code, int32_t K, const qcmet_decode_options *opts,
+                     qcmet_group_plan_t *plan);
 
 /*
  * Index checks of the debug build.  libqcmet_debug.so (the same sources built

@@ -50,7 +50,7 @@ EXPORTS = (
     "qcmet_last_error", "qcmet_status_string", "qcmet_version", "qcmet_decode_noalloc",
     "qcmet_decode_early_stop", "qcmet_minsum_decode", "qcmet_minsum_forward",
     "qcmet_minsum_backward", "qcmet_batch_create", "qcmet_batch_run", "qcmet_batch_get_config",
-    "qcmet_batch_destroy", "qcmet_debug_checks",
+    "qcmet_batch_destroy", "qcmet_debug_checks", "qcmet_group_plan",
 )
 
 
@@ -66,6 +66,13 @@ class CodeInfo(ctypes.Structure):
                 ("circulants", ctypes.c_int32), ("msg_slots", ctypes.c_int32),
                 ("degree1_columns", ctypes.c_int32), ("layers", ctypes.c_int32),
                 ("max_row_degree", ctypes.c_int32), ("merge_mode", ctypes.c_int32)]
+
+
+class GroupPlan(ctypes.Structure):
+    _fields_ = [("cluster_size", ctypes.c_int32), ("groups_per_cluster", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("clusters", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("active_clusters", ctypes.c_int32),
+                ("shared_bytes", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Frame(ctypes.Structure):
@@ -84,7 +91,8 @@ class BatchConfig(ctypes.Structure):
 class DecodeOptions(ctypes.Structure):
     _fields_ = [("msg_format", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("l2_persist", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("cluster_size", ctypes.c_int32), ("groups_per_cluster", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 def _load():
@@ -123,6 +131,7 @@ def _load():
     lib.qcmet_status_string.restype = ctypes.c_char_p
     lib.qcmet_version.argtypes = []
     lib.qcmet_debug_checks.argtypes = [vp]
+    lib.qcmet_group_plan.argtypes = [vp, i32, ctypes.POINTER(DecodeOptions), ctypes.POINTER(GroupPlan)]
     for name in EXPORTS:
         if name not in ("qcmet_code_destroy", "qcmet_last_error", "qcmet_status_string",
                         "qcmet_batch_destroy"):
@@ -150,6 +159,16 @@ def debug_checks() -> int:
     _check(lib.qcmet_debug_checks(ctypes.byref(bits)))
     return int(bits.value)
 
+
+
+def group_plan(code: "Code", K: int, msg: str = "fp32", cluster: int = 0, groups: int = 0) -> dict:
+    """The launch shape of a grouped-kernel decode of K frames on the current
+    device (``qcmet_group_plan``): cluster size, groups per cluster, threads,
+    clusters, blocks, clusters the device holds at once, shared memory."""
+    plan = GroupPlan()
+    opts = _options(msg, 0, False, "group", cluster, groups)
+    _check(lib.qcmet_group_plan(code._h, int(K), ctypes.byref(opts), ctypes.byref(plan)))
+    return {name: int(getattr(plan, name)) for name, _ in GroupPlan._fields_ if name != "reserved"}
 
 
 class Code:
@@ -209,7 +228,7 @@ class Code:
 
 
 def _options(msg: str, threads: int, l2_persist: bool = False, kernel: str = "auto",
-             cluster: int = 0) -> DecodeOptions:
+             cluster: int = 0, groups: int = 0) -> DecodeOptions:
     if msg not in MSG:
         raise ValueError(f"msg must be one of {sorted(MSG)}")
     if kernel not in KERNEL:
@@ -220,12 +239,13 @@ def _options(msg: str, threads: int, l2_persist: bool = False, kernel: str = "au
     o.l2_persist = 1 if l2_persist else 0
     o.kernel = KERNEL[kernel]
     o.cluster_size = int(cluster)
+    o.groups_per_cluster = int(groups)
     return o
 
 
 def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=None,
            msg: str = "fp32", threads: int = 0, stream=None, want_post: bool = True,
-           l2_persist: bool = False, kernel: str = "auto", cluster: int = 0):
+           l2_persist: bool = False, kernel: str = "auto", cluster: int = 0, groups: int = 0):
     """Decode K frames on the GPU (``qcmet_decode_ex``).
 
     ``llr``: float32 CUDA tensor [K, n]; ``syn``: uint8 CUDA tensor [K, m].
@@ -234,7 +254,8 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     The call is asynchronous on ``stream`` (default: torch's current stream).
     ``l2_persist`` keeps the core posteriors in a persisting L2 window.
     ``kernel`` is "auto", "frame" or "group" (``QCMET_KERNEL_*``); ``cluster``
-    the grouped kernel's cluster size (0 = automatic).
+    the grouped kernel's cluster size and ``groups`` its groups of four frames
+    per cluster (0 = automatic).
     """
     import torch
 
@@ -259,7 +280,7 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    opts = _options(msg, threads, l2_persist, kernel, cluster)
+    opts = _options(msg, threads, l2_persist, kernel, cluster, groups)
     _check(lib.qcmet_decode_ex(code.handle, llr.data_ptr(), syn.data_ptr(), K, int(iterations),
                                hard.data_ptr(), llr_post.data_ptr() if llr_post is not None else None,
                                ok.data_ptr(), ctypes.byref(opts), sptr))
@@ -301,7 +322,8 @@ def decode_early_stop(code: Code, llr, syn, max_iterations: int, check_every: in
 
 def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
                 want_post: bool = True, msg: str = "fp32", threads: int = 0, stream=None,
-                out=None, l2_persist: bool = False, kernel: str = "auto", cluster: int = 0):
+                out=None, l2_persist: bool = False, kernel: str = "auto", cluster: int = 0,
+                groups: int = 0):
     """Decode frames held in host memory (``qcmet_decode_host``); synchronous.
 
     ``out`` may supply preallocated (hard, llr_post, ok) host arrays, e.g. pinned.
@@ -317,7 +339,7 @@ def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
     for a, dt in ((llr, np.float32), (syn, np.uint8), (hard, np.uint8), (ok, np.uint8)):
         if a.dtype != dt or not a.flags.c_contiguous:
             raise ValueError("host arrays must be C-contiguous with the documented dtypes")
-    opts = _options(msg, threads, l2_persist, kernel, cluster)
+    opts = _options(msg, threads, l2_persist, kernel, cluster, groups)
     sptr = 0
     if stream is not None:
         sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)

@@ -89,6 +89,7 @@ int grow(void **buf, size_t *have, size_t need, const char *what) {
 struct KernelChoice {
     int32_t kernel = QCMET_KERNEL_AUTO;
     int32_t cluster = 0;
+    int32_t per_cluster = 0;
 };
 
 int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
@@ -101,9 +102,10 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
     if (o->kernel != QCMET_KERNEL_AUTO && o->kernel != QCMET_KERNEL_FRAME &&
         o->kernel != QCMET_KERNEL_GROUP)
         return fail(QCMET_ERR_INVALID_ARG, "unknown kernel");
-    if (o->cluster_size != 0 && o->cluster_size != 1 && o->cluster_size != 2 &&
-        o->cluster_size != 4 && o->cluster_size != 8)
-        return fail(QCMET_ERR_INVALID_ARG, "cluster_size must be 0, 1, 2, 4 or 8");
+    if (o->cluster_size < 0 || o->cluster_size > 16)
+        return fail(QCMET_ERR_INVALID_ARG, "cluster_size must be 0 (automatic) or 1 .. 16");
+    if (o->groups_per_cluster < 0 || o->groups_per_cluster > 2)
+        return fail(QCMET_ERR_INVALID_ARG, "groups_per_cluster must be 0 (automatic), 1 or 2");
     if (o->msg_format != QCMET_MSG_FP32 && o->msg_format != QCMET_MSG_FP16 &&
         o->msg_format != QCMET_MSG_BF16)
         return fail(QCMET_ERR_INVALID_ARG, "unknown msg_format");
@@ -120,6 +122,7 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
     if (kc) {
         kc->kernel = o->kernel;
         kc->cluster = o->cluster_size;
+        kc->per_cluster = o->groups_per_cluster;
     }
     return QCMET_OK;
 }
@@ -161,16 +164,16 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
 }
 
 // The grouped kernel (decode_group.cu) for K frames: interleaved scratch of
-// ceil(K/4) groups, one cluster per group.
+// ceil(K/4) groups, one or two groups per cluster.
 int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, int32_t K,
                  int32_t T, uint8_t *hard, float *llr_post, uint8_t *ok, int32_t fmt,
-                 int32_t cluster, bool l2p, void *stream, const float *w_scale = nullptr,
+                 const KernelChoice &kc, bool l2p, void *stream, const float *w_scale = nullptr,
                  const float *w_offset = nullptr) {
     const int32_t stage_ops = qcmet::group_stage_ops(c);
     qcmet::GroupLaunch L;
     std::string err;
     int st = qcmet::choose_group_launch(fmt, K, c.Z, (int32_t)c.image.words.size(), stage_ops,
-                                        cluster, &L, err, w_scale != nullptr);
+                                        kc.cluster, &L, err, w_scale != nullptr, kc.per_cluster);
     if (st) return fail(st, err);
     const size_t G = (size_t)L.groups;
     const size_t n = (size_t)c.nb * c.Z, m = (size_t)c.mb * c.Z;
@@ -208,8 +211,8 @@ int decode_group(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, i
     a.w_scale = w_scale;
     a.w_offset = w_offset;
     qcmet::TraceRange range("qcmet decode: grouped kernel, %d frames, %d layer groups x %d iterations, "
-                            "%d clusters of %d%s", K, (int)c.layer_first.size() - 1, T, L.groups,
-                            L.cluster, w_scale ? ", min-sum rule" : "");
+                            "%d groups, %d per cluster of %d%s", K, (int)c.layer_first.size() - 1, T,
+                            L.groups, L.per_cluster, L.cluster, w_scale ? ", min-sum rule" : "");
     st = qcmet::launch_decode_group(a, fmt, L, stream, err);
     if (st) return fail(st, err);
     return QCMET_OK;
@@ -241,8 +244,8 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
                     "the grouped kernel serves fixed-iteration decodes only");
     if (kc.kernel == QCMET_KERNEL_GROUP || (kc.kernel == QCMET_KERNEL_AUTO && group_ok &&
                                             use_group_by_default(c, K)))
-        return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc.cluster, l2p,
-                            stream, w_scale, w_offset);
+        return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc, l2p, stream,
+                            w_scale, w_offset);
 
     const size_t n = (size_t)c.nb * c.Z;
     const size_t stride = qcmet::slot_stride(c.Z);
@@ -634,6 +637,34 @@ int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offse
     qcmet::TraceRange range("qcmet min-sum backward: %d frames x %d iterations", a.K, a.T);
     int st = qcmet::launch_learned_backward(a, stream, err);
     if (st) return fail(st, err);
+    return QCMET_OK;
+}
+
+int qcmet_group_plan(const qcmet_code *code, int32_t K, const qcmet_decode_options *opts,
+                     qcmet_group_plan_t *plan) {
+    if (!code || !plan) return fail(QCMET_ERR_INVALID_ARG, "code and plan must not be NULL");
+    if (K < 1) return fail(QCMET_ERR_INVALID_ARG, "need K >= 1");
+    int32_t fmt = 0, threads = 0;
+    KernelChoice kc;
+    int st = check_options(opts, &fmt, &threads, nullptr, &kc);
+    if (st) return st;
+    const qcmet::Code &c = code->c;
+    if ((int64_t)c.nb * qcmet::group_zp(c.Z) > INT32_MAX)
+        return fail(QCMET_ERR_INVALID_ARG, "code too large for the grouped kernel's 32-bit offsets");
+    qcmet::GroupLaunch L;
+    std::string err;
+    st = qcmet::choose_group_launch(fmt, K, c.Z, (int32_t)c.image.words.size(),
+                                    qcmet::group_stage_ops(c), kc.cluster, &L, err, false,
+                                    kc.per_cluster);
+    if (st) return fail(st, err);
+    plan->cluster_size = L.cluster;
+    plan->groups_per_cluster = L.per_cluster;
+    plan->threads_per_block = L.threads;
+    plan->clusters = (L.groups + L.per_cluster - 1) / L.per_cluster;
+    plan->blocks = plan->clusters * L.cluster;
+    plan->active_clusters = L.active_clusters;
+    plan->shared_bytes = (int32_t)L.smem;
+    plan->reserved = 0;
     return QCMET_OK;
 }
 

@@ -9,27 +9,34 @@
 // access is a single aligned 16-byte request whatever the circulant shift,
 // and one thread computes one check for four frames.
 //
-//  * Mapping: a thread-block cluster of C CTAs owns a group of four frames;
-//    CTA r of the cluster owns the checks [r Zc, (r + 1) Zc) of every row
-//    (Zc = ceil(Z / C)).  Rows of one layer share no column, so a layer needs
-//    no synchronisation inside; between layers the posteriors written by one
-//    CTA are read by others, so a layer ends with one cluster barrier
-//    (barrier.cluster arrive.release / wait.acquire).  Cross-CTA data are
-//    read through L2 only (cp.async.cg, ld.global.cg).
-//  * Layouts in library scratch, per group g: channel LLRs [n] float4,
-//    syndrome bits [m] as four bytes, core posteriors [core_cols][Z] float4,
-//    messages [slots][Z] as four FP32 (16 B) or four 16-bit values (8 B).  The
-//    kernel builds the interleaved channel and syndrome from the caller's
-//    frame-major arrays in its prologue and writes the caller's frame-major
-//    outputs in its epilogue.  Degree-1 columns keep no state (their
+//  * Mapping: a thread-block cluster of C CTAs (1 .. 16) owns one or two
+//    groups of four frames.  The groups' checks form one range [0, NG Zp)
+//    (group 1's start at Zp, Z rounded up to 32), and CTA r of the cluster
+//    owns [r Zc, (r + 1) Zc) of it in every row (Zc = ceil(NG Zp / C)
+//    rounded up to 32), so that a CTA may hold checks of both groups; two
+//    groups per cluster let cluster sizes that do not divide the SM count
+//    evenly keep more SMs busy.  Rows of one layer share no column, so a
+//    layer needs no synchronisation inside; between layers the posteriors
+//    written by one CTA are read by others, so a layer ends with one cluster
+//    barrier (barrier.cluster arrive.release / wait.acquire).  Cross-CTA data
+//    are read through L2 only (cp.async.cg, ld.global.cg).  The host picks C
+//    and the groups per cluster from the device's cluster occupancy, to
+//    minimise the checks per SM (times the waves of clusters).
+//  * Layouts in library scratch, per group g: channel LLRs [nb][Zp] float4,
+//    syndrome bits [mb][Zp] as four bytes, core posteriors [core_cols][Zp]
+//    float4, messages [slots][Zp] as four FP32 (16 B) or four 16-bit values
+//    (8 B); every row starts on a 128-byte line.  The kernel builds the
+//    interleaved channel and syndrome from the caller's frame-major arrays
+//    in its prologue and writes the caller's frame-major outputs in its
+//    epilogue.  Degree-1 columns keep no state (their
 //    q = L_qn - L_rmn(old) is the channel LLR exactly); in the last iteration
 //    their posterior replaces the interleaved channel value, which only their
 //    own check reads.
 //  * Rows of degree <= 4: one thread per check, operands of the next rounds
 //    copied into the thread's own shared-memory slots by cp.async while it
 //    computes the current round (no block barrier: each thread reads only the
-//    slots it filled).  Rows of degree 5..16: two lanes per check, each
-//    lane's loads issued together.
+//    slots it filled).  Rows of degree 5..16: two lanes per check; up to
+//    degree 12 each lane stages the next 16 checks' operands the same way.
 //  * The check rule is check_rule.cuh's exclusive-product form, evaluated per
 //    frame in the same operation order as the per-frame kernel, so the two
 //    kernels give bit-identical results.
@@ -37,7 +44,10 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <type_traits>
 
 #include "check_rule.cuh"
@@ -318,7 +328,43 @@ struct GFrame {
     Policies pol;
     Bounds bd;                       // extents for the debug build's index checks
     int zp;                          // row stride of the arrays (Z rounded up to 32)
+    GroupScratch gstride;            // bytes from each array to the next group's
 };
+
+// A cluster that owns two groups numbers their checks (and variables) in one
+// virtual range: group 0's index v at v, group 1's at Zp + v.  Indices Z ..
+// Zp - 1 of a group are padding and stand for no check.
+struct VIndex {
+    int g;    // group within the cluster (0 or 1)
+    int l;    // index within the group; a check or variable when l < Z
+};
+// With one group per cluster (NG = 1) the virtual range is the group's own
+// [0, Z) and both helpers reduce to the identity.
+template <int NG>
+__device__ __forceinline__ VIndex vsplit(int v, int zp) {
+    if constexpr (NG == 1) {
+        return VIndex{0, v};
+    } else {
+        const int g = v >= zp ? 1 : 0;
+        return VIndex{g, v - g * zp};
+    }
+}
+// whether a virtual index stands for a check or variable (not padding)
+template <int NG>
+__device__ __forceinline__ bool real(const VIndex &x, int Z) {
+    return NG == 1 || x.l < Z;
+}
+// p moved from group 0's arrays to group g's (gstride: bytes between the
+// groups' copies of p's array)
+template <int NG, typename T>
+__device__ __forceinline__ T *in_group(T *p, int g, size_t gstride) {
+    if constexpr (NG == 1) {
+        return p;
+    } else {
+        using B = typename std::conditional<std::is_const<T>::value, const char, char>::type;
+        return reinterpret_cast<T *>(reinterpret_cast<B *>(p) + (g ? gstride : 0));
+    }
+}
 
 // The check rule on one check of a row of degree DC + D1 <= 4 (core edges
 // first) for four frames: lv holds the edges' posteriors (channel LLRs for
@@ -409,7 +455,7 @@ __device__ __forceinline__ void small_rule(float4 (&lv)[DC + D1], float4 (&ro)[D
 // (Each row routine is its own function: it runs once per row and layer, and
 // a separate register allocation keeps the rows that a code rarely has from
 // costing the others spills.)
-template <int DC, int D1, typename M, int S, int R>
+template <int DC, int D1, typename M, int S, int R, int NG>
 __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_base,
                                         const GFrame<M> fr, int lo, int hi, int Z, bool first,
                                         bool last, float4 wt) {
@@ -426,10 +472,12 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
     int sh[D];
     V *slot[NC];
     int xo[D], zo[NC];  // variable and slot offsets (index checks of the debug build)
+    size_t vs[D];       // bytes to the next group's copy of the edge's variables
 #pragma unroll
     for (int e = 0; e < D; ++e) {
         const int4 en = ent[e];
         src[e] = (e < DC ? fr.core4 : fr.ch4) + en.x;
+        vs[e] = e < DC ? fr.gstride.core : fr.gstride.ch;
         sh[e] = en.y;
         xo[e] = en.x;
         if (e < DC) {
@@ -438,32 +486,41 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
         }
     }
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
+    const int zp = fr.zp;
     auto issue = [&](int i, int b) {
-        if (i < hi) {
+        const VIndex c = vsplit<NG>(i, zp);
+        if (i < hi && real<NG>(c, Z)) {
             const uint32_t sb = s0 + (uint32_t)b * rb;
 #pragma unroll
             for (int e = 0; e < D; ++e) {
-                int j = i + sh[e];
+                int j = c.l + sh[e];
                 j = j >= Z ? j - Z : j;
                 if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
-                    cp_async16_cg(sb + e * opb, src[e] + j, e < DC ? fr.pol.post : fr.pol.in);
+                    cp_async16_cg(sb + e * opb, in_group<NG>(src[e] + j, c.g, vs[e]),
+                                  e < DC ? fr.pol.post : fr.pol.in);
             }
             if (!first) {
 #pragma unroll
                 for (int e = 0; e < DC; ++e)
-                    if (in_range((long long)zo[e] * fr.zp + i, fr.bd.msgs, kBadSlot))
-                        MV::copy_async(sb + (D + e) * opb, slot[e] + i, fr.pol.msg);
+                    if (in_range((long long)zo[e] * zp + c.l, fr.bd.msgs, kBadSlot))
+                        MV::copy_async(sb + (D + e) * opb,
+                                       in_group<NG>(slot[e] + c.l, c.g, fr.gstride.msg), fr.pol.msg);
             }
         }
         g_commit();
+    };
+    auto syndrome = [&](int i) {
+        const VIndex c = vsplit<NG>(i, zp);
+        return (i < hi && real<NG>(c, Z) &&
+                in_range((long long)check_base + c.l, fr.bd.checks, kBadCheck))
+                   ? ld4(in_group<NG>(fr.syn4 + check_base + c.l, c.g, fr.gstride.syn), fr.pol.in)
+                   : 0u;
     };
     uint32_t sy[S];
 #pragma unroll
     for (int k = 0; k < S - 1; ++k) {
         const int i = lo + tid + k * nt;
-        sy[k] = (i < hi && in_range((long long)check_base + i, fr.bd.checks, kBadCheck))
-                    ? ld4(fr.syn4 + check_base + i, fr.pol.in)
-                    : 0u;
+        sy[k] = syndrome(i);
         issue(i, k);
     }
     int buf = 0;
@@ -472,29 +529,33 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
             const int nx = i + (S - 1) * nt;
             int nb = buf + (S - 1);
             nb = nb >= S ? nb - S : nb;
-            sy[S - 1] = (nx < hi && in_range((long long)check_base + nx, fr.bd.checks, kBadCheck))
-                            ? ld4(fr.syn4 + check_base + nx, fr.pol.in)
-                            : 0u;
+            sy[S - 1] = syndrome(nx);
             issue(nx, nb);
         }
         g_wait<S - 1>();
-        const float4 *sv = qcmet_group_smem + tid + (size_t)buf * (rb / 16);
-        float4 lv[D], ro[NC];
+        const VIndex c = vsplit<NG>(i, zp);
+        if (real<NG>(c, Z)) {
+            const float4 *sv = qcmet_group_smem + tid + (size_t)buf * (rb / 16);
+            float4 lv[D], ro[NC];
 #pragma unroll
-        for (int e = 0; e < D; ++e) lv[e] = sv[(size_t)e * nt];
+            for (int e = 0; e < D; ++e) lv[e] = sv[(size_t)e * nt];
 #pragma unroll
-        for (int e = 0; e < DC; ++e)
-            ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : MV::from_stage(sv + (size_t)(D + e) * nt);
-        small_rule<DC, D1, M, R>(lv, ro, sy[0], last, wt);
+            for (int e = 0; e < DC; ++e)
+                ro[e] = first ? make_float4(0.f, 0.f, 0.f, 0.f)
+                              : MV::from_stage(sv + (size_t)(D + e) * nt);
+            small_rule<DC, D1, M, R>(lv, ro, sy[0], last, wt);
 #pragma unroll
-        for (int e = 0; e < D; ++e) {
-            if (e >= DC && !last) continue;
-            int j = i + sh[e];
-            j = j >= Z ? j - Z : j;
-            if (e < DC && in_range((long long)zo[e < DC ? e : 0] * fr.zp + i, fr.bd.msgs, kBadSlot))
-                MV::store(slot[e < DC ? e : 0] + i, ro[e < DC ? e : 0], fr.pol.msg);
-            if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
-                st16(const_cast<float4 *>(src[e]) + j, lv[e], e < DC ? fr.pol.post : fr.pol.in);
+            for (int e = 0; e < D; ++e) {
+                if (e >= DC && !last) continue;
+                int j = c.l + sh[e];
+                j = j >= Z ? j - Z : j;
+                if (e < DC && in_range((long long)zo[e < DC ? e : 0] * zp + c.l, fr.bd.msgs, kBadSlot))
+                    MV::store(in_group<NG>(slot[e < DC ? e : 0] + c.l, c.g, fr.gstride.msg),
+                              ro[e < DC ? e : 0], fr.pol.msg);
+                if (in_range((long long)xo[e] + j, e < DC ? fr.bd.core : fr.bd.vars, kBadVariable))
+                    st16(in_group<NG>(const_cast<float4 *>(src[e]) + j, c.g, vs[e]), lv[e],
+                         e < DC ? fr.pol.post : fr.pol.in);
+            }
         }
 #pragma unroll
         for (int k = 0; k < S - 1; ++k) sy[k] = sy[k + 1];
@@ -509,7 +570,7 @@ __device__ __noinline__ void grow_small(const int4 *__restrict__ ent, int check_
 // the warp's next 16 checks into its own shared-memory slots (cp.async, two
 // rounds of 2 E slots) while it computes the current ones; otherwise it loads
 // all its edges' operands, then computes.  Both give the same operands.
-template <int D, typename M, int R, bool STAGED>
+template <int D, typename M, int R, bool STAGED, int NG>
 __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_base,
                                        const GFrame<M> fr, int lo, int hi, int Z, bool first,
                                        bool last, float4 wt) {
@@ -525,23 +586,32 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
     // of the lane's edge el, slot E + el its old message
     const uint32_t opb = (uint32_t)nt * 16u;
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(qcmet_group_smem + tid);
+    // an edge's variable j (posterior, or channel LLR of a degree-1 column) and
+    // its message of check l, in group g's arrays
+    auto var_of = [&](const int4 &en, int j, int g) {
+        return in_group<NG>((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j, g,
+                            en.z < 0 ? fr.gstride.ch : fr.gstride.core);
+    };
+    auto msg_of = [&](const int4 &en, int l, int g) {
+        return in_group<NG>(fr.msg4 + (size_t)en.z * (size_t)fr.zp + l, g, fr.gstride.msg);
+    };
     auto issue = [&](int i0, int b) {
         const int i = i0 + (lane & 15);
-        if (i0 < hi && i < hi) {
+        const VIndex c = vsplit<NG>(i, fr.zp);
+        if (i0 < hi && i < hi && real<NG>(c, Z)) {
 #pragma unroll
             for (int el = 0; el < E; ++el) {
                 const int e = part * E + el;
                 if (e >= D) continue;
                 const int4 en = ent[e];
-                int j = i + en.y;
+                int j = c.l + en.y;
                 j = j >= Z ? j - Z : j;
                 const uint32_t sb = s0 + (uint32_t)(b * 2 * E + el) * opb;
                 if (in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable))
-                    cp_async16_cg(sb, (en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
-                                  en.z < 0 ? fr.pol.in : fr.pol.post);
-                if (!first && en.z >= 0 && in_range((long long)en.z * fr.zp + i, fr.bd.msgs, kBadSlot))
-                    MV::copy_async(sb + (uint32_t)E * opb, fr.msg4 + (size_t)en.z * (size_t)fr.zp + i,
-                                   fr.pol.msg);
+                    cp_async16_cg(sb, var_of(en, j, c.g), en.z < 0 ? fr.pol.in : fr.pol.post);
+                if (!first && en.z >= 0 &&
+                    in_range((long long)en.z * fr.zp + c.l, fr.bd.msgs, kBadSlot))
+                    MV::copy_async(sb + (uint32_t)E * opb, msg_of(en, c.l, c.g), fr.pol.msg);
             }
         }
         g_commit();
@@ -550,12 +620,12 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
     int b = 0;
     for (int i0 = lo + warp * 16; i0 < hi; i0 += nwarps * 16) {
         const int i = i0 + (lane & 15);
-        const bool valid = i < hi;
-        const int ic = valid ? i : hi - 1;
+        const VIndex c = vsplit<NG>(i, fr.zp);
+        const bool valid = i < hi && real<NG>(c, Z);
         if constexpr (STAGED) issue(i0 + nwarps * 16, b ^ 1);
         const uint32_t par4 =
-            (part == 0 && in_range((long long)check_base + ic, fr.bd.checks, kBadCheck))
-                ? ld4(fr.syn4 + check_base + ic, fr.pol.in)
+            (valid && part == 0 && in_range((long long)check_base + c.l, fr.bd.checks, kBadCheck))
+                ? ld4(in_group<NG>(fr.syn4 + check_base + c.l, c.g, fr.gstride.syn), fr.pol.in)
                 : 0u;
         float4 lv[E], ro[E];
         if constexpr (STAGED) {
@@ -574,15 +644,15 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             for (int el = 0; el < E; ++el) {
                 const int e = min(part * E + el, D - 1);
                 const int4 en = ent[e];
-                int j = ic + en.y;
+                int j = c.l + en.y;
                 j = j >= Z ? j - Z : j;
-                lv[el] = in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable)
-                             ? ld16((en.z < 0 ? fr.ch4 : fr.core4) + en.x + j,
-                                    en.z < 0 ? fr.pol.in : fr.pol.post)
+                lv[el] = (valid && in_range((long long)en.x + j, en.z < 0 ? fr.bd.vars : fr.bd.core,
+                                            kBadVariable))
+                             ? ld16(var_of(en, j, c.g), en.z < 0 ? fr.pol.in : fr.pol.post)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
-                ro[el] = (!first && en.z >= 0 &&
-                          in_range((long long)en.z * fr.zp + ic, fr.bd.msgs, kBadSlot))
-                             ? MV::load(fr.msg4 + (size_t)en.z * (size_t)fr.zp + ic, fr.pol.msg)
+                ro[el] = (valid && !first && en.z >= 0 &&
+                          in_range((long long)en.z * fr.zp + c.l, fr.bd.msgs, kBadSlot))
+                             ? MV::load(msg_of(en, c.l, c.g), fr.pol.msg)
                              : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -687,21 +757,21 @@ __device__ __noinline__ void grow_pair(const int4 *__restrict__ ent, int check_b
             if (e >= D) continue;
             const int4 en = ent[e];
             if (en.z < 0 && !last) continue;
-            int j = i + en.y;
+            int j = c.l + en.y;
             j = j >= Z ? j - Z : j;
             if (en.z >= 0) {
-                if (in_range((long long)en.z * fr.zp + i, fr.bd.msgs, kBadSlot))
-                    MV::store(fr.msg4 + (size_t)en.z * (size_t)fr.zp + i, ro[el], fr.pol.msg);
+                if (in_range((long long)en.z * fr.zp + c.l, fr.bd.msgs, kBadSlot))
+                    MV::store(msg_of(en, c.l, c.g), ro[el], fr.pol.msg);
                 if (in_range((long long)en.x + j, fr.bd.core, kBadVariable))
-                    st16(fr.core4 + en.x + j, lv[el], fr.pol.post);
+                    st16(var_of(en, j, c.g), lv[el], fr.pol.post);
             } else if (in_range((long long)en.x + j, fr.bd.vars, kBadVariable)) {
-                st16(fr.ch4 + en.x + j, lv[el], fr.pol.in);
+                st16(var_of(en, j, c.g), lv[el], fr.pol.in);
             }
         }
     }
 }
 
-template <typename M, int S, int R>
+template <typename M, int S, int R, int NG>
 __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check_base,
                                           const GFrame<M> &fr, int lo, int hi, int Z, bool first,
                                           bool last, float4 wt) {
@@ -711,7 +781,7 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
         switch (degree * 8 + dc) {
 #define QCMET_GSMALL_CASE(DD, CC)                                                            \
     case DD * 8 + CC:                                                                        \
-        grow_small<CC, DD - CC, M, S, R>(ent, check_base, fr, lo, hi, Z, first, last, wt);   \
+        grow_small<CC, DD - CC, M, S, R, NG>(ent, check_base, fr, lo, hi, Z, first, last, wt); \
         break;
             QCMET_GSMALL_CASE(1, 0)
             QCMET_GSMALL_CASE(1, 1)
@@ -737,7 +807,8 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
 // two rounds: group_stage_ops), higher ones load directly
 #define QCMET_GPAIR_CASE(DD)                                                                         \
     case DD:                                                                                         \
-        grow_pair<DD, M, R, (DD <= kPairStagedMax)>(ent, check_base, fr, lo, hi, Z, first, last, wt); \
+        grow_pair<DD, M, R, (DD <= kPairStagedMax), NG>(ent, check_base, fr, lo, hi, Z, first, last, \
+                                                        wt);                                        \
         break;
         QCMET_GPAIR_CASE(5)
         QCMET_GPAIR_CASE(6)
@@ -756,41 +827,46 @@ __device__ __forceinline__ void gdispatch(int degree, const int4 *ent, int check
     }
 }
 
-// The frames of one group: frame f < nf reads ch[f] [n] and syn[f] [m] and
-// writes post[f] [n] (when not null), hard[f] [n] and ok[f] [1].
+// The frames of the cluster's groups (at most two): frame f < nf[g] of group g
+// reads ch[g][f] [n] and syn[g][f] [m] and writes post[g][f] [n] (when not
+// null), hard[g][f] [n] and ok[g][f] [1].
+constexpr int kMaxGroupsPerCluster = 2;
+template <int NG>
 struct GroupIO {
-    const float *ch[kGF];
-    const uint8_t *syn[kGF];
-    float *post[kGF];
-    uint8_t *hard[kGF];
-    uint8_t *ok[kGF];
-    int nf;
+    const float *ch[NG][kGF];
+    const uint8_t *syn[NG][kGF];
+    float *post[NG][kGF];
+    uint8_t *hard[NG][kGF];
+    uint8_t *ok[NG][kGF];
+    int nf[NG];
+    int ng;  // groups of the cluster (1 .. NG)
 };
 
-
-// One cluster decodes one group (steps 1-4) with the schedule `s` in shared
-// memory; CTA r of the cluster's C owns checks [lo, hi) of every row.  Every
-// thread of every CTA of the cluster executes the same sequence of cluster
-// barriers: one after the prologue, one per layer of every iteration and one
-// before the ok flags are written.  s_fail is a shared word of the calling
-// CTA (rank 0's collects the syndrome-test failures).
+// One cluster decodes its groups (steps 1-4) with the schedule `s` in shared
+// memory.  The cluster's checks (and variables) form the virtual range
+// [0, ng Zp) (vsplit); CTA r of the cluster's C owns [lo, hi) of it in every
+// row.  Every thread of every CTA of the cluster executes the same sequence
+// of cluster barriers: one after the prologue, one per layer of every
+// iteration and one before the ok flags are written.  s_fail points to two
+// shared words of the calling CTA (rank 0's collect each group's
+// syndrome-test failures).
 //   w_scale, w_offset: min-sum weights [T][mb][2] (R == kGroupMinSum)
-template <typename M, int S, int R>
-__device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO &io, GFrame<M> fr,
+template <typename M, int S, int R, int NG>
+__device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<NG> &io, GFrame<M> fr,
                                                   int T, int r, int C, unsigned *s_fail,
                                                   const float *w_scale = nullptr,
                                                   const float *w_offset = nullptr) {
     const int nt = blockDim.x;
     const int tid = threadIdx.x;
     const int Z = s.Z;
-    const size_t zp = (size_t)fr.zp;
-    // checks per CTA, a multiple of 32: every warp's 32 checks then start on
+    const int zp = fr.zp;
+    // indices per CTA, a multiple of 32: every warp's 32 checks then start on
     // a 128-byte line of the message and syndrome rows
-    const int Zc = ((Z + C - 1) / C + 31) / 32 * 32;
-    const int lo = min(Z, r * Zc);
-    const int hi = min(Z, lo + Zc);
-    const int nf = io.nf;
-    if (r == 0 && tid == 0) *s_fail = 0u;
+    const int span = NG == 1 ? Z : io.ng * zp;
+    const int Zc = ((span + C - 1) / C + 31) / 32 * 32;
+    const int lo = min(span, r * Zc);
+    const int hi = min(span, lo + Zc);
+    if (r == 0 && tid < kMaxGroupsPerCluster) s_fail[tid] = 0u;
 
     // Step 1 and the interleaved copies of this CTA's share: variables
     // [lo, hi) of every column, checks [lo, hi) of every row.  Lanes past nf
@@ -801,25 +877,31 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
         const size_t cb = (size_t)c * Z;  // caller's frame-major arrays
         const size_t gb = (size_t)c * zp;
         for (int v = lo + tid; v < hi; v += nt) {
-            float x[kGF];
+            const VIndex x = vsplit<NG>(v, zp);
+            if (!real<NG>(x, Z)) continue;
+            float y[kGF];
 #pragma unroll
-            for (int f = 0; f < kGF; ++f) x[f] = f < nf ? __ldcs(io.ch[f] + cb + v) : 1.0f;
-            const float4 x4 = make_float4(x[0], x[1], x[2], x[3]);
-            if (in_range((long long)gb + v, fr.bd.vars, kBadVariable)) fr.ch4[gb + v] = x4;
-            if (core && in_range((long long)cc * zp + v, fr.bd.core, kBadVariable))
-                fr.core4[(size_t)cc * zp + v] = x4;
+            for (int f = 0; f < kGF; ++f)
+                y[f] = f < io.nf[x.g] ? __ldcs(io.ch[x.g][f] + cb + x.l) : 1.0f;
+            const float4 y4 = make_float4(y[0], y[1], y[2], y[3]);
+            if (in_range((long long)gb + x.l, fr.bd.vars, kBadVariable))
+                *in_group<NG>(fr.ch4 + gb + x.l, x.g, fr.gstride.ch) = y4;
+            if (core && in_range((long long)cc * zp + x.l, fr.bd.core, kBadVariable))
+                *in_group<NG>(fr.core4 + (size_t)cc * zp + x.l, x.g, fr.gstride.core) = y4;
         }
     }
     for (int l = 0; l < s.mb; ++l) {
         const size_t lb = (size_t)l * Z;
         const size_t gl = (size_t)l * zp;
         for (int i = lo + tid; i < hi; i += nt) {
+            const VIndex x = vsplit<NG>(i, zp);
+            if (!real<NG>(x, Z)) continue;
             uint32_t w = 0u;
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
-                if (f < nf) w |= (uint32_t)(__ldcs(io.syn[f] + lb + i) & 1u) << (8 * f);
-            if (in_range((long long)gl + i, fr.bd.checks, kBadCheck))
-                const_cast<uint32_t *>(fr.syn4)[gl + i] = w;
+                if (f < io.nf[x.g]) w |= (uint32_t)(__ldcs(io.syn[x.g][f] + lb + x.l) & 1u) << (8 * f);
+            if (in_range((long long)gl + x.l, fr.bd.checks, kBadCheck))
+                *in_group<NG>(const_cast<uint32_t *>(fr.syn4) + gl + x.l, x.g, fr.gstride.syn) = w;
         }
     }
     cluster_sync();
@@ -837,7 +919,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
                     wt = make_float4(__ldg(w_scale + w), __ldg(w_scale + w + 1), __ldg(w_offset + w),
                                      __ldg(w_offset + w + 1));
                 }
-                gdispatch<M, S, R>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last, wt);
+                gdispatch<M, S, R, NG>(row.y, s.entries + row.x, row.z, fr, lo, hi, Z, first, last, wt);
             }
             cluster_sync();
         }
@@ -851,57 +933,77 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO 
         const size_t cb = (size_t)c * Z;
         const size_t gb = (size_t)c * zp;
         for (int v = lo + tid; v < hi; v += nt) {
-            const bool ok = core ? in_range((long long)cc * zp + v, fr.bd.core, kBadVariable)
-                                 : in_range((long long)gb + v, fr.bd.vars, kBadVariable);
+            const VIndex x = vsplit<NG>(v, zp);
+            if (!real<NG>(x, Z)) continue;
+            const bool ok = core ? in_range((long long)cc * zp + x.l, fr.bd.core, kBadVariable)
+                                 : in_range((long long)gb + x.l, fr.bd.vars, kBadVariable);
             const float4 L4 = !ok  ? make_float4(0.f, 0.f, 0.f, 0.f)
-                              : core ? __ldcg(fr.core4 + (size_t)cc * zp + v)
-                                     : __ldcg(fr.ch4 + gb + v);
+                              : core ? __ldcg(in_group<NG>(fr.core4 + (size_t)cc * zp + x.l, x.g,
+                                                           fr.gstride.core))
+                                     : __ldcg(in_group<NG>(fr.ch4 + gb + x.l, x.g, fr.gstride.ch));
 #pragma unroll
             for (int f = 0; f < kGF; ++f) {
-                if (f >= nf) break;
+                if (f >= io.nf[x.g]) break;
                 const float L = comp(L4, f);
-                if (io.post[f]) io.post[f][cb + v] = L;
-                io.hard[f][cb + v] = L < 0.0f ? 1 : 0;
+                if (io.post[x.g][f]) io.post[x.g][f][cb + x.l] = L;
+                io.hard[x.g][f][cb + x.l] = L < 0.0f ? 1 : 0;
             }
         }
     }
-    uint32_t bad = 0u;
+    uint32_t bad[NG] = {};
+    // the syndrome word of check x of the row whose first check is row_first
+    auto syn_word = [&](const VIndex &x, size_t row_first) {
+        return in_range((long long)row_first + x.l, fr.bd.checks, kBadCheck)
+                   ? *in_group<NG>(fr.syn4 + row_first + x.l, x.g, fr.gstride.syn)
+                   : 0u;
+    };
     for (int zr = 0; zr < s.n_zero_rows; ++zr) {
         const size_t lb = (size_t)s.zero_rows[zr] * zp;
-        for (int i = lo + tid; i < hi; i += nt)
-            if (in_range((long long)lb + i, fr.bd.checks, kBadCheck)) bad |= fr.syn4[lb + i];
+        for (int i = lo + tid; i < hi; i += nt) {
+            const VIndex x = vsplit<NG>(i, zp);
+            if (real<NG>(x, Z)) bad[x.g] |= syn_word(x, lb);
+        }
     }
     for (int j = 0; j < s.n_rows; ++j) {
         const int4 row = s.rows[j];
         const int4 *ent = s.entries + row.x;
         for (int i = lo + tid; i < hi; i += nt) {
-            uint32_t p = in_range((long long)row.z + i, fr.bd.checks, kBadCheck) ? fr.syn4[row.z + i] : 0u;
+            const VIndex x = vsplit<NG>(i, zp);
+            if (!real<NG>(x, Z)) continue;
+            uint32_t p = syn_word(x, (size_t)row.z);
             for (int e = 0; e < row.y; ++e) {
                 const int4 en = ent[e];
-                int jj = i + en.y;
+                int jj = x.l + en.y;
                 jj = jj >= Z ? jj - Z : jj;
                 if (in_range((long long)en.x + jj, en.z < 0 ? fr.bd.vars : fr.bd.core, kBadVariable))
-                    p ^= sign_bytes(__ldcg((en.z < 0 ? fr.ch4 : fr.core4) + en.x + jj));
+                    p ^= sign_bytes(__ldcg(in_group<NG>((en.z < 0 ? fr.ch4 : fr.core4) + en.x + jj, x.g,
+                                                        en.z < 0 ? fr.gstride.ch : fr.gstride.core)));
             }
-            bad |= p;
+            bad[x.g] |= p;
         }
     }
-    bad = __reduce_or_sync(0xffffffffu, bad & 0x01010101u);
-    if ((tid & 31) == 0 && bad) {
-        uint32_t local = (uint32_t)__cvta_generic_to_shared(s_fail);
-        uint32_t remote;
-        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0));
-        asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(remote), "r"(bad)
-                     : "memory");
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const uint32_t b = __reduce_or_sync(0xffffffffu, bad[g] & 0x01010101u);
+        if ((tid & 31) == 0 && b) {
+            uint32_t local = (uint32_t)__cvta_generic_to_shared(s_fail + g);
+            uint32_t remote;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(0));
+            asm volatile("red.relaxed.cluster.shared::cluster.or.b32 [%0], %1;" ::"r"(remote), "r"(b)
+                         : "memory");
+        }
     }
     cluster_sync();
-    if (r == 0 && tid < nf) io.ok[tid][0] = ((*s_fail >> (8 * tid)) & 1u) ? 0 : 1;
+    if (r == 0 && tid < io.ng * kGF) {
+        const int g = tid / kGF, f = tid % kGF;
+        if (f < io.nf[g]) io.ok[g][f][0] = ((s_fail[g] >> (8 * f)) & 1u) ? 0 : 1;
+    }
 }
 
 // Views of one group's scratch for the code of schedule s.
 template <typename M>
 __device__ __forceinline__ GFrame<M> group_scratch(const Sched &s, void *ch4, uint32_t *syn4,
-                                                   void *core4, void *msgs4) {
+                                                   void *core4, void *msgs4, GroupScratch gstride) {
     GFrame<M> fr;
     fr.ch4 = static_cast<float4 *>(ch4);
     fr.syn4 = syn4;
@@ -910,6 +1012,7 @@ __device__ __forceinline__ GFrame<M> group_scratch(const Sched &s, void *ch4, ui
     fr.pol = make_policies<std::is_same<M, float>::value ? QCMET_GROUP_HINT_FP32
                                                           : QCMET_GROUP_HINT_16BIT>();
     fr.zp = (s.Z + 31) & ~31;
+    fr.gstride = gstride;
     fr.bd.core = (long long)s.core_cols * fr.zp;
     fr.bd.vars = (long long)s.nb * fr.zp;
     fr.bd.msgs = (long long)s.msg_slots * fr.zp;
@@ -943,40 +1046,46 @@ __device__ __forceinline__ void load_group_image(int32_t *sw, const int32_t *ima
     __syncthreads();
 }
 
-// K frames of one code: cluster g decodes frames 4g .. 4g + 3.
+// K frames of one code: cluster k owns groups NG k .. NG k + NG - 1 (NG = 1 or
+// 2 groups per cluster); group g holds frames 4g .. 4g + 3.
 //   S    : rounds staged per thread (S - 1 in flight while one is computed)
 //   NT   : largest block (launch bound); MINB: blocks per SM the bound asks for
 // Shared memory: the staging area, S * stage_ops * blockDim 16-byte slots
-// (stage_ops = the most operands a check of a row of degree <= 4 stages),
-// then the layer table.
-template <typename M, int S, int NT, int MINB, int R = kGroupSumProduct>
+// (group_stage_ops), then the layer table.
+template <typename M, int S, int NT, int MINB, int R, int NG>
 __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs a) {
     const int C = (int)cluster_nctarank();
     const int r = (int)cluster_ctarank();
-    const int g = (int)cluster_idx();
-    __shared__ unsigned s_fail;
+    const int k = (int)cluster_idx();
+    __shared__ unsigned s_fail[kMaxGroupsPerCluster];
     int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * a.stage_ops * blockDim.x);
     load_group_image(sw, a.image, a.image_words);
     const Sched s = make_sched(sw);
     const size_t n = (size_t)a.n, m = (size_t)a.m;
-    const int f0 = g * kGF;
-    GroupIO io;
-    io.nf = min(kGF, a.K - f0);
+    const int groups = (a.K + kGF - 1) / kGF;
+    const int g0 = k * NG;
+    GroupIO<NG> io;
+    io.ng = min(NG, groups - g0);
 #pragma unroll
-    for (int f = 0; f < kGF; ++f) {
-        const bool have = f < io.nf;
-        io.ch[f] = have ? a.ch + (size_t)(f0 + f) * n : nullptr;
-        io.syn[f] = have ? a.syn + (size_t)(f0 + f) * m : nullptr;
-        io.post[f] = (have && a.post) ? a.post + (size_t)(f0 + f) * n : nullptr;
-        io.hard[f] = have ? a.hard + (size_t)(f0 + f) * n : nullptr;
-        io.ok[f] = have ? a.ok + f0 + f : nullptr;
+    for (int g = 0; g < NG; ++g) {
+        const int f0 = (g0 + g) * kGF;
+        io.nf[g] = g < io.ng ? min(kGF, a.K - f0) : 0;
+#pragma unroll
+        for (int f = 0; f < kGF; ++f) {
+            const bool have = f < io.nf[g];
+            io.ch[g][f] = have ? a.ch + (size_t)(f0 + f) * n : nullptr;
+            io.syn[g][f] = have ? a.syn + (size_t)(f0 + f) * m : nullptr;
+            io.post[g][f] = (have && a.post) ? a.post + (size_t)(f0 + f) * n : nullptr;
+            io.hard[g][f] = have ? a.hard + (size_t)(f0 + f) * n : nullptr;
+            io.ok[g][f] = have ? a.ok + f0 + f : nullptr;
+        }
     }
     GFrame<M> fr = group_scratch<M>(
-        s, static_cast<char *>(a.ch4) + (size_t)g * a.g_bytes.ch,
-        reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(a.syn4) + (size_t)g * a.g_bytes.syn),
-        static_cast<char *>(a.core4) + (size_t)g * a.g_bytes.core,
-        static_cast<char *>(a.msgs4) + (size_t)g * a.g_bytes.msg);
-    decode_group_body<M, S, R>(s, io, fr, a.T, r, C, &s_fail, a.w_scale, a.w_offset);
+        s, static_cast<char *>(a.ch4) + (size_t)g0 * a.g_bytes.ch,
+        reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(a.syn4) + (size_t)g0 * a.g_bytes.syn),
+        static_cast<char *>(a.core4) + (size_t)g0 * a.g_bytes.core,
+        static_cast<char *>(a.msgs4) + (size_t)g0 * a.g_bytes.msg, a.g_bytes);
+    decode_group_body<M, S, R, NG>(s, io, fr, a.T, r, C, s_fail, a.w_scale, a.w_offset);
 }
 
 // Mixed batches: persistent clusters take groups (up to four frames of one
@@ -988,7 +1097,7 @@ template <typename M, int S, int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const GroupBatchArgs b) {
     const int C = (int)cluster_nctarank();
     const int r = (int)cluster_ctarank();
-    __shared__ unsigned s_fail;
+    __shared__ unsigned s_fail[kMaxGroupsPerCluster];
     __shared__ int s_job;
     int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * b.stage_ops * blockDim.x);
     int cur_code = -1;
@@ -1010,35 +1119,47 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
             cur_code = jb.code_id;
         }
         const Sched s = make_sched(sw);
-        GroupIO io;
-        io.nf = jb.nf;
+        GroupIO<1> io;
+        io.ng = 1;
+        io.nf[0] = jb.nf;
 #pragma unroll
         for (int f = 0; f < kGF; ++f) {
-            io.ch[f] = jb.ch[f];
-            io.syn[f] = jb.syn[f];
-            io.post[f] = jb.post[f];
-            io.hard[f] = jb.hard[f];
-            io.ok[f] = jb.ok[f];
+            io.ch[0][f] = jb.ch[f];
+            io.syn[0][f] = jb.syn[f];
+            io.post[0][f] = jb.post[f];
+            io.hard[0][f] = jb.hard[f];
+            io.ok[0][f] = jb.ok[f];
         }
-        GFrame<M> fr = group_scratch<M>(s, jb.ch4, jb.syn4, jb.core4, jb.msgs4);
-        decode_group_body<M, S, kGroupSumProduct>(s, io, fr, b.T, r, C, &s_fail);
+        GFrame<M> fr = group_scratch<M>(s, jb.ch4, jb.syn4, jb.core4, jb.msgs4, GroupScratch{});
+        decode_group_body<M, S, kGroupSumProduct, 1>(s, io, fr, b.T, r, C, s_fail);
     }
 }
 
 // Launch variants of the kernel: (rounds staged, block bound, blocks per SM).
 struct Variant {
     int S, NT, MINB;
-    const void *kern[4];  // by message format (sum-product); [3]: min-sum, FP32 messages
+    // [message format (sum-product); 3: min-sum, FP32 messages][groups per cluster - 1]
+    const void *kern[4][kMaxGroupsPerCluster];
 };
+
+template <int S, int NT, int MINB, int NG>
+void fill_variant(Variant &v) {
+    v.kern[0][NG - 1] =
+        reinterpret_cast<const void *>(&decode_group_kernel<float, S, NT, MINB, kGroupSumProduct, NG>);
+    v.kern[1][NG - 1] =
+        reinterpret_cast<const void *>(&decode_group_kernel<__half, S, NT, MINB, kGroupSumProduct, NG>);
+    v.kern[2][NG - 1] = reinterpret_cast<const void *>(
+        &decode_group_kernel<__nv_bfloat16, S, NT, MINB, kGroupSumProduct, NG>);
+    v.kern[3][NG - 1] =
+        reinterpret_cast<const void *>(&decode_group_kernel<float, S, NT, MINB, kGroupMinSum, NG>);
+}
 
 template <int S, int NT, int MINB>
 Variant make_variant() {
-    return Variant{S, NT, MINB,
-                   {reinterpret_cast<const void *>(&decode_group_kernel<float, S, NT, MINB>),
-                    reinterpret_cast<const void *>(&decode_group_kernel<__half, S, NT, MINB>),
-                    reinterpret_cast<const void *>(&decode_group_kernel<__nv_bfloat16, S, NT, MINB>),
-                    reinterpret_cast<const void *>(
-                        &decode_group_kernel<float, S, NT, MINB, kGroupMinSum>)}};
+    Variant v{S, NT, MINB, {}};
+    fill_variant<S, NT, MINB, 1>(v);
+    fill_variant<S, NT, MINB, 2>(v);
+    return v;
 }
 
 const Variant *variants(int *count) {
@@ -1072,9 +1193,25 @@ size_t group_msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 16 : 8; }
 #define QCMET_GROUP_VARIANT (-1)
 #endif
 
+namespace {
+// Launch shapes chosen so far, by (device, format, K, Z, table size, stage_ops,
+// requested cluster size and groups per cluster, rule): the choice queries the occupancy of up to 64
+// shapes, which a repeated decode of the same shape should not pay again.
+struct LaunchKey {
+    int dev, fmt, K, Z, image_words, stage_ops, want, want_ng, minsum;
+    bool operator<(const LaunchKey &o) const {
+        return std::tie(dev, fmt, K, Z, image_words, stage_ops, want, want_ng, minsum) <
+               std::tie(o.dev, o.fmt, o.K, o.Z, o.image_words, o.stage_ops, o.want, o.want_ng,
+                        o.minsum);
+    }
+};
+std::mutex g_launch_mu;
+std::map<LaunchKey, GroupLaunch> g_launch_cache;
+}  // namespace
+
 int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
                         int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
-                        std::string &err, bool minsum) {
+                        std::string &err, bool minsum, int32_t want_per_cluster) {
     if (fmt != QCMET_MSG_FP32 && fmt != QCMET_MSG_FP16 && fmt != QCMET_MSG_BF16) {
         err = "unknown message format";
         return QCMET_ERR_INVALID_ARG;
@@ -1083,70 +1220,94 @@ int choose_group_launch(int32_t fmt, int32_t K, int32_t Z, int32_t image_words,
         err = "the min-sum rule keeps FP32 messages";
         return QCMET_ERR_INVALID_ARG;
     }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        err = "no CUDA device";
+        return QCMET_ERR_CUDA;
+    }
+    const LaunchKey key{dev,       fmt,          K, Z, image_words, stage_ops, want_cluster,
+                        want_per_cluster, minsum ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lock(g_launch_mu);
+        auto it = g_launch_cache.find(key);
+        if (it != g_launch_cache.end()) {
+            *out = it->second;
+            return QCMET_OK;
+        }
+    }
     const int kidx = minsum ? 3 : fmt;
     const int G = (K + kGF - 1) / kGF;
+    const int zp = (int)group_zp(Z);
     int nv = 0;
     const Variant *var = variants(&nv);
-    // candidate cluster sizes: the requested one, else 1, 2, 4, 8 with at
-    // least 128 checks per CTA
-    int cands[4], nc = 0;
-    if (want_cluster > 0) {
-        cands[nc++] = want_cluster;
-    } else {
-        for (int c = 1; c <= 8; c *= 2)
-            if (c == 1 || (Z + c - 1) / c >= 128) cands[nc++] = c;
-    }
     double best = 0.0;
     bool have = false;
     for (int vi = 0; vi < nv; ++vi) {
         if (QCMET_GROUP_VARIANT >= 0 && vi != QCMET_GROUP_VARIANT) continue;
-        const void *kern = var[vi].kern[kidx];
-        for (int k = 0; k < nc; ++k) {
-            const int C = cands[k];
-            const int zc = (Z + C - 1) / C;
-            const int threads = group_threads(zc, var[vi].NT);
-            const size_t smem = group_smem(var[vi].S, threads, stage_ops, image_words);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                continue;
-            }
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3((unsigned)(G * C));
-            cfg.blockDim = dim3((unsigned)threads);
-            cfg.dynamicSmemBytes = smem;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = (unsigned)C;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int active = 0;
-            e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
-            if (e != cudaSuccess || active <= 0) {
-                cudaGetLastError();
-                continue;
-            }
-            // An SM moves the operands of a fixed number of checks per unit of
-            // time, so the decode takes ~ waves of clusters x checks per SM:
-            // zc per block, twice that when two blocks share an SM.
-            const int waves = (G + active - 1) / active;
-            const double cost = (double)waves * zc * var[vi].MINB + 1e-3 * vi;
-            if (!have || cost < best) {
-                best = cost;
-                have = true;
-                out->cluster = C;
-                out->threads = threads;
-                out->groups = G;
-                out->active_clusters = active;
-                out->smem = smem;
-                out->variant = vi;
-                out->kidx = kidx;
-                out->stage_ops = stage_ops;
+        for (int ng = 1; ng <= kMaxGroupsPerCluster && ng <= G; ++ng) {
+            if (want_per_cluster > 0 && ng != want_per_cluster) continue;
+            const void *kern = var[vi].kern[kidx][ng - 1];
+            const int clusters = (G + ng - 1) / ng;
+            // cluster sizes: the requested one, else 1 .. 16 with at least 128
+            // checks per CTA (sizes above 8 are non-portable)
+            for (int C = 1; C <= 16; ++C) {
+                if (want_cluster > 0 ? C != want_cluster : (C > 1 && ng * Z / C < 128)) continue;
+                const int zc = ((ng * zp + C - 1) / C + 31) / 32 * 32;
+                const int threads = group_threads(zc, var[vi].NT);
+                const size_t smem = group_smem(var[vi].S, threads, stage_ops, image_words);
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
+                if (e == cudaSuccess && C > 8)
+                    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(clusters * C));
+                cfg.blockDim = dim3((unsigned)threads);
+                cfg.dynamicSmemBytes = smem;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)C;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int active = 0;
+                e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
+                if (e != cudaSuccess || active <= 0) {
+                    cudaGetLastError();
+                    continue;
+                }
+                // An SM moves the operands of a fixed number of checks per unit
+                // of time, so the decode takes ~ waves of clusters x checks per
+                // SM: zc per block, twice that when two blocks share an SM.  Ties
+                // go to one group per cluster, smaller clusters, the first variant.
+                const int waves = (clusters + active - 1) / active;
+                const double cost = (double)waves * zc * var[vi].MINB *
+                                        (1.0 + 1e-4 * (ng - 1) + 1e-5 * C) +
+                                    1e-3 * vi;
+                if (!have || cost < best) {
+                    best = cost;
+                    have = true;
+                    out->cluster = C;
+                    out->per_cluster = ng;
+                    out->threads = threads;
+                    out->groups = G;
+                    out->active_clusters = active;
+                    out->smem = smem;
+                    out->variant = vi;
+                    out->kidx = kidx;
+                    out->stage_ops = stage_ops;
+                }
             }
         }
+    }
+    if (have) {
+        std::lock_guard<std::mutex> lock(g_launch_mu);
+        g_launch_cache[key] = *out;
     }
     if (!have) {
         err = want_cluster > 0 ? "cluster size " + std::to_string(want_cluster) +
@@ -1268,18 +1429,27 @@ int launch_decode_group(const GroupArgs &a, int32_t fmt, const GroupLaunch &L, v
     int nv = 0;
     const Variant *var = variants(&nv);
     if (fmt < 0 || fmt > 2 || L.variant < 0 || L.variant >= nv || a.stage_ops != L.stage_ops ||
-        L.kidx < 0 || L.kidx > 3 || (L.kidx == 3) != (a.w_scale != nullptr)) {
+        L.kidx < 0 || L.kidx > 3 || (L.kidx == 3) != (a.w_scale != nullptr) ||
+        L.per_cluster < 1 || L.per_cluster > kMaxGroupsPerCluster) {
         err = "invalid grouped launch";
         return QCMET_ERR_INVALID_ARG;
     }
-    const void *kern = var[L.variant].kern[L.kidx];
+    const void *kern = var[L.variant].kern[L.kidx][L.per_cluster - 1];
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem);
     if (e != cudaSuccess) {
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
         return QCMET_ERR_UNSUPPORTED;
     }
+    if (L.cluster > 8) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) {
+            err = std::string("cudaFuncSetAttribute(non-portable cluster): ") + cudaGetErrorString(e);
+            return QCMET_ERR_UNSUPPORTED;
+        }
+    }
+    const int clusters = (L.groups + L.per_cluster - 1) / L.per_cluster;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(L.groups * L.cluster));
+    cfg.gridDim = dim3((unsigned)(clusters * L.cluster));
     cfg.blockDim = dim3((unsigned)L.threads);
     cfg.dynamicSmemBytes = L.smem;
     cfg.stream = static_cast<cudaStream_t>(stream);

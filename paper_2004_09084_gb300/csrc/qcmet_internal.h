@@ -237,9 +237,11 @@ struct GroupArgs {
     const float *w_offset;
 };
 
-// Launch shape of the grouped kernel: `groups` clusters of `cluster` CTAs.
+// Launch shape of the grouped kernel: clusters of `cluster` CTAs, each owning
+// `per_cluster` of the `groups` groups.
 struct GroupLaunch {
     int32_t cluster = 0;
+    int32_t per_cluster = 1;
     int32_t threads = 0;
     int32_t groups = 0;
     int32_t active_clusters = 0;  // clusters of this shape the device holds at once
@@ -293,11 +295,12 @@ int32_t group_stage_ops(const Code &c);
 
 // Bytes of one group's message for one check and slot (four frames).
 size_t group_msg_bytes(int32_t msg_format);
-// Pick the cluster size (want_cluster > 0 forces it), kernel build and block
-// size for K frames of a code with expansion Z.
+// Pick the cluster size (want_cluster > 0 forces it), the groups per cluster
+// (want_per_cluster > 0 forces it), kernel build and block size for K frames
+// of a code with expansion Z.
 int choose_group_launch(int32_t msg_format, int32_t K, int32_t Z, int32_t image_words,
                         int32_t stage_ops, int32_t want_cluster, GroupLaunch *out,
-                        std::string &err, bool minsum = false);
+                        std::string &err, bool minsum = false, int32_t want_per_cluster = 0);
 int launch_decode_group(const GroupArgs &a, int32_t msg_format, const GroupLaunch &L,
                         void *stream, std::string &err, size_t window_bytes = 0,
                         float hit_ratio = 0.0f);

@@ -170,9 +170,10 @@ def test_group_kernel_rejects_what_it_does_not_serve(q, small):
     with pytest.raises(q.QcmetError) as e:
         q.decode_early_stop(qc, d, s, 10, 1, kernel="group")
     assert e.value.status == q.ERR_UNSUPPORTED
-    with pytest.raises(q.QcmetError) as e:
-        q.decode(qc, d, s, 3, kernel="group", cluster=3)
-    assert e.value.status == q.ERR_INVALID_ARG
+    for bad in (17, -1):
+        with pytest.raises(q.QcmetError) as e:
+            q.decode(qc, d, s, 3, kernel="group", cluster=bad)
+        assert e.value.status == q.ERR_INVALID_ARG
 
 
 # --------------------------------------------------------------------------
@@ -189,3 +190,54 @@ def test_group_kernel_full_size(q):
     assert_same((h, p, ok), run(q, qc, fr.llr, fr.syn, 2, kernel="frame"))
     for cluster in (1, 8):
         assert_same((h, p, ok), run(q, qc, fr.llr, fr.syn, 2, kernel="group", cluster=cluster))
+
+
+# --------------------------------------------------------------------------
+# Launch shapes: any cluster size up to 16 and two groups per cluster (the
+# cluster's blocks split the two groups' checks, so one block may hold checks
+# of both) give the per-frame kernel's results bit for bit.
+
+@pytest.mark.parametrize("rate,Z,K,cluster,groups", [
+    ("0.1", 1250, 16, 3, 2),     # two groups per cluster, blocks straddle the groups
+    ("0.1", 1250, 12, 5, 2),     # three groups: the last cluster holds one
+    ("0.05", 1000, 9, 4, 2),     # a partial last group (one frame)
+    ("0.02", 777, 8, 7, 2),      # Z with no factor of 2
+    ("0.1", 1250, 8, 9, 1),      # a non-portable cluster size, one group per cluster
+    ("0.1", 1250, 4, 16, 1),     # the largest cluster
+    ("0.05", 1000, 24, 6, 0),    # automatic groups per cluster
+])
+def test_launch_shapes_are_bit_identical_to_the_frame_kernel(q, rate, Z, K, cluster, groups):
+    code = synth.make_code(rate, Z)
+    fr = synth.make_frames(code, K, synth.RATE_SNR[rate] + 0.05, first=900)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    try:
+        plan = q.group_plan(qc, K, cluster=cluster, groups=groups)
+    except q.QcmetError as e:
+        assert e.status == q.ERR_UNSUPPORTED
+        pytest.skip(f"cluster size {cluster} cannot be scheduled on this device")
+    if groups:
+        assert plan["groups_per_cluster"] == groups
+    assert plan["cluster_size"] == cluster
+    for msg in ("fp32", "fp16"):
+        for T in (1, 8):
+            ref = run(q, qc, fr.llr, fr.syn, T, kernel="frame", msg=msg)
+            got = run(q, qc, fr.llr, fr.syn, T, kernel="group", cluster=cluster, groups=groups,
+                      msg=msg)
+            assert_same(got, ref)
+
+
+def test_group_plan_spreads_frames_over_the_device(q):
+    code = synth.make_code("0.1", 12500)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for K in (4, 16, 64, 128):
+        p = q.group_plan(qc, K)
+        groups = (K + 3) // 4
+        assert p["clusters"] == -(-groups // p["groups_per_cluster"])
+        assert p["blocks"] == p["clusters"] * p["cluster_size"]
+        assert p["clusters"] <= p["active_clusters"], p      # one wave
+        # a group of four frames is split over several SMs when SMs are free
+        assert p["blocks"] >= min(sms // 2, 8 * groups), p
+    with pytest.raises(q.QcmetError) as e:
+        q.group_plan(qc, 8, groups=3)
+    assert e.value.status == q.ERR_INVALID_ARG
