@@ -329,7 +329,8 @@ int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offse
  * code in the batch, stored interleaved in the plan's scratch) from a work
  * counter.  Autotuning (autotune != 0) times, on this batch with
  * min(iterations, 12) iterations, every combination of kernel and its size
- * (block of 512 or 1024 threads; cluster of 2, 4 or 8 blocks), layer schedule
+ * (block of 512 or 1024 threads; cluster of 2, 4, 5, 8 or 16 blocks, sizes the
+ * device cannot hold skipped), layer schedule
  * (each code's own, or the other schedule that gives identical results:
  * base-row order <-> merged rows, Results Eqs. (m1), (m2)) and work order
  * (largest first, or as given), and keeps the fastest.  All candidates give

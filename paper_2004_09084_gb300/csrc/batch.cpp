@@ -317,9 +317,9 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
     }
 
     // candidates (all give the same results): the per-frame kernel with block
-    // size 512 or 1024, the grouped kernel with clusters of 2, 4 or 8 blocks;
-    // each with the codes' own schedule or the other exact one, and the work
-    // taken largest first or as given
+    // size 512 or 1024, the grouped kernel with clusters of 2, 4, 5, 8 or 16
+    // blocks; each with the codes' own schedule or the other exact one, and
+    // the work taken largest first or as given
     struct Cand { int32_t kernel; int32_t size; bool alt; bool largest; };
     std::vector<Cand> cands;
     const bool have_alt =
@@ -327,7 +327,7 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
     if (autotune) {
         for (int32_t kern : {QCMET_KERNEL_FRAME, QCMET_KERNEL_GROUP})
             for (int32_t size : kern == QCMET_KERNEL_FRAME ? std::vector<int32_t>{512, 1024}
-                                                          : std::vector<int32_t>{2, 4, 8})
+                                                          : std::vector<int32_t>{2, 4, 5, 8, 16})
                 for (bool alt : {false, true})
                     for (bool lf : {true, false})
                         if (!alt || have_alt) cands.push_back({kern, size, alt, lf});

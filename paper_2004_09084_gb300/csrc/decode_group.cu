@@ -1378,7 +1378,7 @@ int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t clus
                        : fmt == QCMET_MSG_FP16 ? group_batch_kernel_ptr<__half>()
                        : fmt == QCMET_MSG_BF16 ? group_batch_kernel_ptr<__nv_bfloat16>()
                                                : nullptr;
-    if (!kern || cluster < 1 || cluster > 8 || max_Z < 1) {
+    if (!kern || cluster < 1 || cluster > 16 || max_Z < 1) {
         err = "invalid grouped batch launch";
         return QCMET_ERR_INVALID_ARG;
     }
@@ -1387,6 +1387,8 @@ int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t clus
     const int threads = group_threads((max_Z + C - 1) / C, 512);
     const size_t smem = group_smem(kGroupStages, threads, b.stage_ops, max_image_words);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) {
         cudaGetLastError();
         err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
