@@ -255,3 +255,24 @@ def test_grouped_minsum_equals_the_frame_kernel(q, learned, Z, T):
         h2, p2, ok2 = learned.decode(qc, llr[k:k + 2].contiguous(), syn[k:k + 2].contiguous(), ws, wo)
         torch.cuda.synchronize()
         assert torch.equal(p[k:k + 2], p2) and torch.equal(h[k:k + 2], h2) and torch.equal(ok[k:k + 2], ok2)
+
+
+def test_grouped_minsum_with_two_groups_per_cluster(q, learned):
+    # 192 frames of the full-size code: the launch chooser gives a cluster two
+    # groups when that leaves fewer checks per SM; frames of both groups of a
+    # cluster (blocks that straddle them included) equal the frame kernel's
+    code = synth.make_code("0.1", 12500)
+    qc = q.Code(code.base, code.shifts, code.Z)
+    plan = q.group_plan(qc, 192)
+    if plan["groups_per_cluster"] != 2:
+        pytest.skip(f"the chooser keeps one group per cluster on this device: {plan}")
+    T = 3
+    fr = synth.make_frames(code, 192, 0.2, first=1200)
+    ws, wo = weights(code, T, seed=6)
+    ws, wo = torch.from_numpy(ws).cuda(), torch.from_numpy(wo).cuda()
+    llr, syn = torch.from_numpy(fr.llr).cuda(), torch.from_numpy(fr.syn).cuda()
+    h, p, ok = learned.decode(qc, llr, syn, ws, wo)
+    for k in (0, 4, 6, 186, 190):
+        h2, p2, ok2 = learned.decode(qc, llr[k:k + 2].contiguous(), syn[k:k + 2].contiguous(), ws, wo)
+        torch.cuda.synchronize()
+        assert torch.equal(p[k:k + 2], p2) and torch.equal(h[k:k + 2], h2) and torch.equal(ok[k:k + 2], ok2)
