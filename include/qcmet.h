@@ -327,16 +327,21 @@ int qcmet_minsum_backward(const qcmet_code *code, float *g_scale, float *g_offse
  * counter, and the grouped kernel, whose persistent thread-block clusters
  * take groups of up to four frames of one code (consecutive frames of that
  * code in the batch, stored interleaved in the plan's scratch) from a work
- * counter.  Autotuning (autotune != 0) times, on this batch with
+ * counter.  Autotuning (autotune = 1) times, on this batch with
  * min(iterations, 12) iterations, every combination of kernel and its size
  * (block of 512 or 1024 threads; cluster of 2, 4, 5, 8 or 16 blocks, sizes the
- * device cannot hold skipped), layer schedule
+ * device cannot hold skipped; or the grouped kernel as one concurrent launch
+ * per code, each code's groups given a cluster size and one or two blocks per
+ * SM so that all codes share the device's SMs and finish together), layer schedule
  * (each code's own, or the other schedule that gives identical results:
  * base-row order <-> merged rows, Results Eqs. (m1), (m2)) and work order
- * (largest first, or as given), and keeps the fastest.  All candidates give
+ * (largest first, or as given), times the four fastest again with
+ * min(iterations, 100) iterations, and keeps the fastest.  All candidates give
  * the same results, so the choice affects time only.  Autotuning runs trial
  * decodes, so the inputs must be valid and the outputs writable at creation.
- * Without autotuning the plan takes the grouped kernel with clusters of 4.
+ * Without autotuning (autotune = 0) the plan takes the grouped kernel with
+ * clusters of 4; autotune = 2 takes the per-code concurrent launches without
+ * timing anything.
  */
 typedef struct {
     const qcmet_code *code;   /* the frame's code                          */
@@ -354,10 +359,13 @@ typedef struct {
     int32_t alternate_schedule;  /* 1: the codes' other exact schedule was faster       */
     int32_t largest_first;       /* 1: work is taken in decreasing edge count          */
     int32_t candidates;          /* configurations timed (1 without autotuning)        */
-    float trial_ms;              /* time of two trial decodes of the winner (-1 if none) */
+    float trial_ms;              /* the winner's trial time: one decode of min(iterations,
+                                    100) iterations (two of 12 when iterations <= 12;
+                                    -1 if nothing was timed)                          */
     int32_t kernel;              /* QCMET_KERNEL_FRAME or QCMET_KERNEL_GROUP            */
-    int32_t cluster_size;        /* grouped kernel: blocks per cluster (else 0)         */
-    int32_t reserved[1];
+    int32_t cluster_size;        /* grouped kernel, one launch: blocks per cluster (else 0) */
+    int32_t per_code_launches;   /* grouped kernel, one concurrent launch per code: the
+                                    number of launches (else 0)                        */
 } qcmet_batch_config;
 
 /* frames: host array [K] (copied); msg_format: QCMET_MSG_*.  Pointers must be

@@ -85,7 +85,7 @@ class BatchConfig(ctypes.Structure):
     _fields_ = [("threads_per_block", ctypes.c_int32), ("alternate_schedule", ctypes.c_int32),
                 ("largest_first", ctypes.c_int32), ("candidates", ctypes.c_int32),
                 ("trial_ms", ctypes.c_float), ("kernel", ctypes.c_int32),
-                ("cluster_size", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("cluster_size", ctypes.c_int32), ("per_code_launches", ctypes.c_int32)]
 
 
 class DecodeOptions(ctypes.Structure):
@@ -351,15 +351,18 @@ def decode_host(code: Code, llr: np.ndarray, syn: np.ndarray, iterations: int,
 
 
 class Batch:
-    """A mixed batch plan (``qcmet_batch_*``): frames of several codes, one launch.
+    """A mixed batch plan (``qcmet_batch_*``): frames of several codes in one
+    captured graph (one launch, or one concurrent launch per code).
 
     ``frames`` is a list of ``(code, llr, syn)`` with CUDA tensors of that
     code's sizes.  Outputs are allocated here (``self.hard``, ``self.post``,
     ``self.ok``); :meth:`run` replays the captured graph.  Keep the input
-    tensors alive and write new data into them to decode again.
+    tensors alive and write new data into them to decode again.  ``autotune``:
+    True (1) times every configuration, False (0) takes the grouped kernel with
+    clusters of 4, 2 takes one concurrent launch per code without timing.
     """
 
-    def __init__(self, frames, iterations: int, msg: str = "fp32", autotune: bool = True,
+    def __init__(self, frames, iterations: int, msg: str = "fp32", autotune=True,
                  stream=None, want_post: bool = True):
         import torch
         self._keep = []
@@ -385,7 +388,7 @@ class Batch:
             stream = torch.cuda.current_stream()
         self._stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         _check(lib.qcmet_batch_create(arr, len(frames), int(iterations), MSG[msg],
-                                      1 if autotune else 0, self._stream, ctypes.byref(self._h)))
+                                      int(autotune), self._stream, ctypes.byref(self._h)))
 
     def run(self, stream=None):
         s = self._stream if stream is None else (

@@ -840,6 +840,28 @@ struct GroupIO {
     uint8_t *ok[NG][kGF];
     int nf[NG];
     int ng;  // groups of the cluster (1 .. NG)
+    __device__ int groups() const { return ng; }
+    __device__ int nf_of(int g) const { return nf[g]; }
+    __device__ const float *ch_of(int g, int f) const { return ch[g][f]; }
+    __device__ const uint8_t *syn_of(int g, int f) const { return syn[g][f]; }
+    __device__ float *post_of(int g, int f) const { return post[g][f]; }
+    __device__ uint8_t *hard_of(int g, int f) const { return hard[g][f]; }
+    __device__ uint8_t *ok_of(int g, int f) const { return ok[g][f]; }
+};
+
+// The same accessors over a batch job in global memory: the pointers are read
+// where the prologue and epilogue use them, so that the persistent kernel
+// keeps none of them in registers through the layer loop.
+struct JobIO {
+    const GroupJob *jb;
+    int ng;
+    __device__ int groups() const { return ng; }
+    __device__ int nf_of(int g) const { return g < ng ? jb->nf[g] : 0; }
+    __device__ const float *ch_of(int g, int f) const { return jb->ch[g][f]; }
+    __device__ const uint8_t *syn_of(int g, int f) const { return jb->syn[g][f]; }
+    __device__ float *post_of(int g, int f) const { return jb->post[g][f]; }
+    __device__ uint8_t *hard_of(int g, int f) const { return jb->hard[g][f]; }
+    __device__ uint8_t *ok_of(int g, int f) const { return jb->ok[g][f]; }
 };
 
 // One cluster decodes its groups (steps 1-4) with the schedule `s` in shared
@@ -851,8 +873,8 @@ struct GroupIO {
 // shared words of the calling CTA (rank 0's collect each group's
 // syndrome-test failures).
 //   w_scale, w_offset: min-sum weights [T][mb][2] (R == kGroupMinSum)
-template <typename M, int S, int R, int NG>
-__device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<NG> &io, GFrame<M> fr,
+template <typename M, int S, int R, int NG, typename IO>
+__device__ __forceinline__ void decode_group_body(const Sched &s, const IO &io, GFrame<M> fr,
                                                   int T, int r, int C, unsigned *s_fail,
                                                   const float *w_scale = nullptr,
                                                   const float *w_offset = nullptr) {
@@ -862,7 +884,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<
     const int zp = fr.zp;
     // indices per CTA, a multiple of 32: every warp's 32 checks then start on
     // a 128-byte line of the message and syndrome rows
-    const int span = NG == 1 ? Z : io.ng * zp;
+    const int span = NG == 1 ? Z : io.groups() * zp;
     const int Zc = ((span + C - 1) / C + 31) / 32 * 32;
     const int lo = min(span, r * Zc);
     const int hi = min(span, lo + Zc);
@@ -882,7 +904,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<
             float y[kGF];
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
-                y[f] = f < io.nf[x.g] ? __ldcs(io.ch[x.g][f] + cb + x.l) : 1.0f;
+                y[f] = f < io.nf_of(x.g) ? __ldcs(io.ch_of(x.g, f) + cb + x.l) : 1.0f;
             const float4 y4 = make_float4(y[0], y[1], y[2], y[3]);
             if (in_range((long long)gb + x.l, fr.bd.vars, kBadVariable))
                 *in_group<NG>(fr.ch4 + gb + x.l, x.g, fr.gstride.ch) = y4;
@@ -899,7 +921,7 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<
             uint32_t w = 0u;
 #pragma unroll
             for (int f = 0; f < kGF; ++f)
-                if (f < io.nf[x.g]) w |= (uint32_t)(__ldcs(io.syn[x.g][f] + lb + x.l) & 1u) << (8 * f);
+                if (f < io.nf_of(x.g)) w |= (uint32_t)(__ldcs(io.syn_of(x.g, f) + lb + x.l) & 1u) << (8 * f);
             if (in_range((long long)gl + x.l, fr.bd.checks, kBadCheck))
                 *in_group<NG>(const_cast<uint32_t *>(fr.syn4) + gl + x.l, x.g, fr.gstride.syn) = w;
         }
@@ -943,10 +965,10 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<
                                      : __ldcg(in_group<NG>(fr.ch4 + gb + x.l, x.g, fr.gstride.ch));
 #pragma unroll
             for (int f = 0; f < kGF; ++f) {
-                if (f >= io.nf[x.g]) break;
+                if (f >= io.nf_of(x.g)) break;
                 const float L = comp(L4, f);
-                if (io.post[x.g][f]) io.post[x.g][f][cb + x.l] = L;
-                io.hard[x.g][f][cb + x.l] = L < 0.0f ? 1 : 0;
+                if (io.post_of(x.g, f)) io.post_of(x.g, f)[cb + x.l] = L;
+                io.hard_of(x.g, f)[cb + x.l] = L < 0.0f ? 1 : 0;
             }
         }
     }
@@ -994,9 +1016,9 @@ __device__ __forceinline__ void decode_group_body(const Sched &s, const GroupIO<
         }
     }
     cluster_sync();
-    if (r == 0 && tid < io.ng * kGF) {
+    if (r == 0 && tid < io.groups() * kGF) {
         const int g = tid / kGF, f = tid % kGF;
-        if (f < io.nf[g]) io.ok[g][f][0] = ((s_fail[g] >> (8 * f)) & 1u) ? 0 : 1;
+        if (f < io.nf_of(g)) io.ok_of(g, f)[0] = ((s_fail[g] >> (8 * f)) & 1u) ? 0 : 1;
     }
 }
 
@@ -1088,18 +1110,41 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_kernel(const GroupArgs 
     decode_group_body<M, S, R, NG>(s, io, fr, a.T, r, C, s_fail, a.w_scale, a.w_offset);
 }
 
-// Mixed batches: persistent clusters take groups (up to four frames of one
-// code) from an atomic counter in the order given -- a work queue, nothing
-// waits on another cluster -- reload the layer table when the code changes,
-// and decode the group.  Rank 0 takes the next job and the others read it
-// from rank 0's shared memory.
-template <typename M, int S, int NT, int MINB>
+// Mixed batches: persistent clusters take jobs (one or two groups of up to
+// four frames of one code; NG = the most groups a job holds) from an atomic
+// counter in the order given -- a work queue, nothing waits on another
+// cluster -- reload the layer table when the code changes, and decode the
+// job.  Rank 0 takes the next job and the others read it from rank 0's
+// shared memory.
+// One job with the layer table of its code in shared memory (sw).  A function
+// of its own: the persistent loop's state is saved once around it instead of
+// staying live through the layer loop.
+template <typename M, int S, int NG>
+__device__ __noinline__ void decode_job(const GroupJob &jb, const int32_t *sw, int T, int r, int C,
+                                        unsigned *s_fail) {
+    const Sched s = make_sched(sw);
+    const JobIO io{&jb, min(NG, jb.ng)};
+    GFrame<M> fr = group_scratch<M>(s, jb.ch4, jb.syn4, jb.core4, jb.msgs4, jb.gstride);
+    decode_group_body<M, S, kGroupSumProduct, NG>(s, io, fr, T, r, C, s_fail);
+}
+
+// PERSIST = false: one job per cluster (cluster k decodes the k-th job of the
+// order, the grid holding a cluster per job).
+template <typename M, int S, int NT, int MINB, int NG, bool PERSIST>
 __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const GroupBatchArgs b) {
     const int C = (int)cluster_nctarank();
     const int r = (int)cluster_ctarank();
     __shared__ unsigned s_fail[kMaxGroupsPerCluster];
     __shared__ int s_job;
     int32_t *sw = reinterpret_cast<int32_t *>(qcmet_group_smem + (size_t)S * b.stage_ops * blockDim.x);
+    if constexpr (!PERSIST) {
+        const int k = (int)cluster_idx();
+        if (k >= b.J) return;   // every block of the cluster leaves together
+        const GroupJob &jb = b.jobs[b.order[k]];
+        load_group_image(sw, jb.image, jb.image_words);
+        decode_job<M, S, NG>(jb, sw, b.T, r, C, s_fail);
+        return;
+    }
     int cur_code = -1;
     for (;;) {
         if (r == 0 && threadIdx.x == 0) s_job = atomicAdd(b.counter, 1);
@@ -1118,20 +1163,7 @@ __global__ void __launch_bounds__(NT, MINB) decode_group_batch_kernel(const Grou
             load_group_image(sw, jb.image, jb.image_words);
             cur_code = jb.code_id;
         }
-        const Sched s = make_sched(sw);
-        GroupIO<1> io;
-        io.ng = 1;
-        io.nf[0] = jb.nf;
-#pragma unroll
-        for (int f = 0; f < kGF; ++f) {
-            io.ch[0][f] = jb.ch[f];
-            io.syn[0][f] = jb.syn[f];
-            io.post[0][f] = jb.post[f];
-            io.hard[0][f] = jb.hard[f];
-            io.ok[0][f] = jb.ok[f];
-        }
-        GFrame<M> fr = group_scratch<M>(s, jb.ch4, jb.syn4, jb.core4, jb.msgs4, GroupScratch{});
-        decode_group_body<M, S, kGroupSumProduct, 1>(s, io, fr, b.T, r, C, s_fail);
+        decode_job<M, S, NG>(jb, sw, b.T, r, C, s_fail);
     }
 }
 
@@ -1366,25 +1398,42 @@ GroupScratch group_scratch_bytes(const Code &c, int32_t fmt) {
 }
 
 namespace {
+// persistent clusters over jobs of one group; or one cluster per job of one
+// or two groups
 template <typename M>
-const void *group_batch_kernel_ptr() {
-    return reinterpret_cast<const void *>(&decode_group_batch_kernel<M, kGroupStages, 512, 1>);
+const void *group_batch_kernel_ptr(int ng, bool persistent) {
+    using K = const void *;
+    if (persistent)
+        return reinterpret_cast<K>(&decode_group_batch_kernel<M, kGroupStages, 512, 1, 1, true>);
+    return ng == 2
+               ? reinterpret_cast<K>(&decode_group_batch_kernel<M, kGroupStages, 512, 1, 2, false>)
+               : reinterpret_cast<K>(&decode_group_batch_kernel<M, kGroupStages, 512, 1, 1, false>);
 }
 }  // namespace
 
 int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t cluster, int32_t max_Z,
-                              int32_t max_image_words, void *stream, std::string &err) {
-    const void *kern = fmt == QCMET_MSG_FP32   ? group_batch_kernel_ptr<float>()
-                       : fmt == QCMET_MSG_FP16 ? group_batch_kernel_ptr<__half>()
-                       : fmt == QCMET_MSG_BF16 ? group_batch_kernel_ptr<__nv_bfloat16>()
+                              int32_t max_image_words, void *stream, std::string &err,
+                              int32_t groups_per_job, bool cluster_per_job) {
+    const int ng = groups_per_job == 2 ? 2 : 1;
+    const bool persistent = !cluster_per_job;
+    if (persistent && ng != 1) {
+        err = "persistent grouped batch clusters take jobs of one group";
+        return QCMET_ERR_INVALID_ARG;
+    }
+    const void *kern = fmt == QCMET_MSG_FP32   ? group_batch_kernel_ptr<float>(ng, persistent)
+                       : fmt == QCMET_MSG_FP16 ? group_batch_kernel_ptr<__half>(ng, persistent)
+                       : fmt == QCMET_MSG_BF16 ? group_batch_kernel_ptr<__nv_bfloat16>(ng, persistent)
                                                : nullptr;
-    if (!kern || cluster < 1 || cluster > 16 || max_Z < 1) {
+    if (!kern || cluster < 1 || cluster > 16 || max_Z < 1 ||
+        (groups_per_job != 1 && groups_per_job != 2)) {
         err = "invalid grouped batch launch";
         return QCMET_ERR_INVALID_ARG;
     }
     if (b.J <= 0) return QCMET_OK;
     const int C = cluster;
-    const int threads = group_threads((max_Z + C - 1) / C, 512);
+    // a job's checks: ng groups of Zp (Z rounded up to 32) each
+    const int span = ng == 1 ? max_Z : ng * (int)group_zp(max_Z);
+    const int threads = group_threads((span + C - 1) / C, 512);
     const size_t smem = group_smem(kGroupStages, threads, b.stage_ops, max_image_words);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess && C > 8)
@@ -1405,7 +1454,6 @@ int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t clus
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // persistent clusters: as many as the device holds at once, at most one per job
     cfg.gridDim = dim3((unsigned)(b.J * C));
     int active = 0;
     e = cudaOccupancyMaxActiveClusters(&active, kern, &cfg);
@@ -1414,7 +1462,9 @@ int launch_decode_group_batch(const GroupBatchArgs &b, int32_t fmt, int32_t clus
         err = "cluster size " + std::to_string(C) + " cannot be scheduled for this batch";
         return QCMET_ERR_UNSUPPORTED;
     }
-    const int clusters = active < b.J ? active : b.J;
+    // persistent clusters: as many as the device holds at once, at most one
+    // per job; else one cluster per job
+    const int clusters = persistent && active < b.J ? active : b.J;
     cfg.gridDim = dim3((unsigned)(clusters * C));
     void *args[] = {const_cast<GroupBatchArgs *>(&b)};
     e = cudaLaunchKernelExC(&cfg, kern, args);

@@ -251,23 +251,26 @@ struct GroupLaunch {
     size_t smem = 0;
 };
 
-// One job of a mixed batch on the grouped kernel: up to four frames of one
-// code, stored interleaved in the job's own scratch.
+// One job of a mixed batch on the grouped kernel: one or two groups of up to
+// four frames of one code, stored interleaved in the jobs' own scratch.  With
+// two groups, group 1's arrays follow group 0's at `gstride` bytes per array.
 struct GroupJob {
     const int32_t *image;    // the code's schedule image (device)
     int32_t image_words;
     int32_t code_id;         // jobs with equal code_id share the image
-    int32_t nf;              // frames in the group (1..4)
+    int32_t nf[2];           // frames in each group (1..4; 0 for an absent group 1)
+    int32_t ng;              // groups in the job (1 or 2)
     int32_t pad;
-    const float *ch[4];      // per frame [n]
-    const uint8_t *syn[4];   // per frame [m]
-    float *post[4];          // per frame [n], or nullptr
-    uint8_t *hard[4];        // per frame [n]
-    uint8_t *ok[4];          // per frame [1]
-    void *ch4;               // [nb][Zp] float4
-    uint32_t *syn4;          // [mb][Zp]
-    void *core4;             // [core_cols][Zp] float4
-    void *msgs4;             // [msg_slots][Zp] messages
+    const float *ch[2][4];   // per group and frame [n]
+    const uint8_t *syn[2][4];  // per group and frame [m]
+    float *post[2][4];       // per group and frame [n], or nullptr
+    uint8_t *hard[2][4];     // per group and frame [n]
+    uint8_t *ok[2][4];       // per group and frame [1]
+    void *ch4;               // group 0's [nb][Zp] float4
+    uint32_t *syn4;          // group 0's [mb][Zp]
+    void *core4;             // group 0's [core_cols][Zp] float4
+    void *msgs4;             // group 0's [msg_slots][Zp] messages
+    GroupScratch gstride;    // bytes from group 0's arrays to group 1's
 };
 
 struct GroupBatchArgs {
@@ -279,11 +282,14 @@ struct GroupBatchArgs {
 };
 
 // One launch of the grouped batch kernel with clusters of `cluster` blocks
-// sized for expansion factors up to max_Z; -8 (UNSUPPORTED) when that cluster
-// size cannot be scheduled.
+// sized for expansion factors up to max_Z and jobs of up to groups_per_job
+// groups (1 or 2): persistent clusters taking jobs from the counter (jobs of
+// one group), or with cluster_per_job one cluster per job; -8 (UNSUPPORTED)
+// when that cluster size cannot be scheduled.
 int launch_decode_group_batch(const GroupBatchArgs &b, int32_t msg_format, int32_t cluster,
                               int32_t max_Z, int32_t max_image_words, void *stream,
-                              std::string &err);
+                              std::string &err, int32_t groups_per_job = 1,
+                              bool cluster_per_job = false);
 
 // Debug build: read and clear the index-check words of the two kernel files.
 int take_violations_frame(uint32_t *bits, std::string &err);

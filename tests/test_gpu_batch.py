@@ -35,7 +35,7 @@ def mixed(q, counts):
 
 
 @pytest.mark.parametrize("msg", ["fp32", "fp16"])
-@pytest.mark.parametrize("autotune", [False, True])
+@pytest.mark.parametrize("autotune", [0, 1, 2])
 def test_batch_equals_per_code_decoding(q, msg, autotune):
     frames = mixed(q, [("0.1", 40, 5), ("0.05", 64, 4), ("0.02", 16, 6), ("0.1", 128, 3)])
     T = 12
@@ -44,11 +44,14 @@ def test_batch_equals_per_code_decoding(q, msg, autotune):
     torch.cuda.synchronize()
     cfg = b.config()
     # autotuned: frame kernel (2 block sizes) and grouped kernel (5 cluster
-    # sizes), each x 2 schedules x 2 orders; else the grouped kernel, clusters of 4
-    assert cfg["candidates"] == (28 if autotune else 1)
+    # sizes), each x 2 schedules x 2 orders, and one concurrent launch per code
+    # x 2 schedules; 0: the grouped kernel, clusters of 4; 2: one launch per code
+    assert cfg["candidates"] == {0: 1, 1: 30, 2: 1}[autotune]
     assert cfg["kernel"] in (1, 2)
-    if not autotune:
-        assert cfg["kernel"] == 2 and cfg["cluster_size"] == 4
+    if autotune == 0:
+        assert cfg["kernel"] == 2 and cfg["cluster_size"] == 4 and cfg["per_code_launches"] == 0
+    if autotune == 2:
+        assert cfg["kernel"] == 2 and cfg["per_code_launches"] == 4
     for k, (qc, llr, syn, x) in enumerate(frames):
         h, p, ok = q.decode(qc, llr[None].contiguous(), syn[None].contiguous(), T, msg=msg)
         torch.cuda.synchronize()
