@@ -264,9 +264,9 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
  * KiB) from host memory into the array with cudaMemcpyAsync on `stream`.
  *
  * Set-up: the first call on each device (with that device current) looks up
- * the array's device address with cudaGetSymbolAddress and keeps it for that
- * device's CUDA context; make that first call before any stream capture
- * begins.  A new context on the device (e.g. after cudaDeviceReset) is
+ * the array's device address with cudaGetSymbolAddress, a synchronous runtime
+ * call, and keeps it for that device's CUDA context.  A new context on the
+ * device (e.g. after cudaDeviceReset) is
  * detected by its context id, and the next call looks the address up again.
  * The array itself is placed in device memory when CUDA loads the library's
  * device code on that device (by default, lazily, at the library's first
