@@ -266,8 +266,8 @@ int qcmet_decode_host(const qcmet_code *code, const float *llr_ch, const uint8_t
  * Set-up: the first call on each device (with that device current) looks up
  * the array's device address with cudaGetSymbolAddress, a synchronous runtime
  * call, and keeps it for that device's CUDA context.  A new context on the
- * device (e.g. after cudaDeviceReset) is
- * detected by its context id, and the next call looks the address up again.
+ * device (e.g. after cudaDeviceReset) is detected by its context id, and the
+ * next call looks the address up again.
  * The array itself is placed in device memory when CUDA loads the library's
  * device code on that device (by default, lazily, at the library's first
  * kernel launch or symbol lookup there), not by this call.
