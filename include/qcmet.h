@@ -151,7 +151,8 @@ int qcmet_code_get_schedule(const qcmet_code *code, int32_t *rows, int32_t *laye
  *     (the streamed messages, channel and syndrome evict first, so that the
  *     core posteriors stay in L2) and ignores l2_persist.
  *  QCMET_KERNEL_AUTO (0) -- the grouped kernel for fixed-iteration
- *     sum-product decodes of at least four frames, else the frame kernel.
+ *     sum-product decodes of any number of frames and for min-sum decodes of
+ *     at least four frames, else the frame kernel.
  */
 #define QCMET_KERNEL_AUTO 0
 #define QCMET_KERNEL_FRAME 1

@@ -30,13 +30,17 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// QCMET_KERNEL_AUTO: the grouped kernel for fixed-iteration sum-product
-// decodes of at least four frames (measured at 128 frames of the rate-0.1
-// Z = 12500 code: 7 % faster with FP32 messages, 15-20 % with FP16); the
-// per-frame kernel otherwise.
-bool use_group_by_default(const qcmet::Code &c, int32_t K) {
-    (void)c;
-    return K >= 4;
+// QCMET_KERNEL_AUTO: the grouped kernel for fixed-iteration decodes (measured
+// at 128 frames of the rate-0.1 Z = 12500 code: 7 % faster than the per-frame
+// kernel with FP32 messages, 15-20 % with FP16).  It spreads even one partial
+// group of frames over a cluster of up to 16 SMs, where the per-frame kernel
+// gives each frame one SM, so it serves sum-product decodes of any K; the
+// learned min-sum decode keeps the per-frame kernel below four frames.  Codes
+// whose padded rows overflow the grouped kernel's 32-bit offsets go to the
+// per-frame kernel.
+bool use_group_by_default(const qcmet::Code &c, int32_t K, bool minsum) {
+    if ((int64_t)c.nb * qcmet::group_zp(c.Z) > INT32_MAX) return false;
+    return minsum ? K >= 4 : K >= 1;
 }
 
 size_t msg_bytes(int32_t fmt) { return fmt == QCMET_MSG_FP32 ? 4 : 2; }
@@ -242,8 +246,8 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     if (kc.kernel == QCMET_KERNEL_GROUP && !group_ok)
         return fail(QCMET_ERR_UNSUPPORTED,
                     "the grouped kernel serves fixed-iteration decodes only");
-    if (kc.kernel == QCMET_KERNEL_GROUP || (kc.kernel == QCMET_KERNEL_AUTO && group_ok &&
-                                            use_group_by_default(c, K)))
+    if (kc.kernel == QCMET_KERNEL_GROUP ||
+        (kc.kernel == QCMET_KERNEL_AUTO && group_ok && use_group_by_default(c, K, w_scale != nullptr)))
         return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc, l2p, stream,
                             w_scale, w_offset);
 
