@@ -39,9 +39,10 @@ struct qcmet_batch {
     qcmet::BatchFrame *d_frames = nullptr;
     int32_t *d_order = nullptr;
     int32_t *d_counter = nullptr;
-    // grouped kernel: jobs of up to four frames of one code
-    std::vector<std::vector<int32_t>> job_frames;   // frames of each job
-    void *d_group = nullptr;                        // per-job interleaved scratch, jobs, order
+    // grouped kernel: groups of up to four frames of one code (the groups of a
+    // code consecutive); a job holds one group, or two with per-code launches
+    std::vector<std::vector<int32_t>> job_frames;   // frames of each group
+    void *d_group = nullptr;                        // per-group interleaved scratch, jobs, order
     qcmet::GroupJob *d_jobs = nullptr;
     int32_t *d_jorder = nullptr;
     // grouped kernel, one concurrent launch per code: shapes, work counters,
