@@ -6,9 +6,11 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
+#include "l2_persist.h"
 #include "qcmet_internal.h"
 #include "trace.h"
 
@@ -137,10 +139,13 @@ int check_options(const qcmet_decode_options *o, int32_t *fmt, int32_t *threads,
 // that fits in that part.  No window (window = 0) on a device without
 // persisting L2, or when one window cannot cover the whole state: measured on
 // GB300, a window over a quarter of 512 MB of core posteriors doubled the
-// decode time, while states up to the 128 MiB window gained.
-int l2_window(size_t bytes, size_t *window, float *hit) {
+// decode time, while states up to the 128 MiB window gained.  *raised tells
+// whether the limit was raised, and *prior_limit what it was before.
+int l2_window(size_t bytes, size_t *window, float *hit, bool *raised, size_t *prior_limit) {
     *window = 0;
     *hit = 0.0f;
+    *raised = false;
+    *prior_limit = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
@@ -159,6 +164,8 @@ int l2_window(size_t bytes, size_t *window, float *hit) {
     if (limit < want) {
         e = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want);
         if (e != cudaSuccess) return cuda_fail("cudaDeviceSetLimit(persisting L2)", e);
+        *raised = true;
+        *prior_limit = limit;
         e = cudaDeviceGetLimit(&limit, cudaLimitPersistingL2CacheSize);
         if (e != cudaSuccess) return cuda_fail("cudaDeviceGetLimit(persisting L2)", e);
     }
@@ -247,9 +254,11 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
         return fail(QCMET_ERR_UNSUPPORTED,
                     "the grouped kernel serves fixed-iteration decodes only");
     if (kc.kernel == QCMET_KERNEL_GROUP ||
-        (kc.kernel == QCMET_KERNEL_AUTO && group_ok && use_group_by_default(c, K, w_scale != nullptr)))
+        (kc.kernel == QCMET_KERNEL_AUTO && group_ok && use_group_by_default(c, K, w_scale != nullptr))) {
+        qcmet::release_persisting_l2();
         return decode_group(c, llr_ch, syndrome, K, T, hard, llr_post, ok, fmt, kc, l2p, stream,
                             w_scale, w_offset);
+    }
 
     const size_t n = (size_t)c.nb * c.Z;
     const size_t stride = qcmet::slot_stride(c.Z);
@@ -274,9 +283,13 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
     size_t window = 0;
     float hit = 0.0f;
     if (l2p) {
-        st = l2_window(need_core, &window, &hit);
+        bool raised = false;
+        size_t prior = 0;
+        st = l2_window(need_core, &window, &hit, &raised, &prior);
+        if (raised || window > 0) qcmet::note_persisting_l2(raised, prior);
         if (st) return st;
     }
+    if (window == 0) qcmet::release_persisting_l2();
 
     qcmet::DecodeArgs a;
     a.ch = llr_ch;
@@ -314,6 +327,54 @@ int decode_device(qcmet::Code &c, const float *llr_ch, const uint8_t *syndrome, 
 }  // namespace
 
 namespace qcmet {
+namespace {
+// Per device: whether a windowed launch was issued since the last release,
+// and the persisting-L2 size to put back where the library raised it.
+struct L2State {
+    bool windowed = false;
+    bool raised = false;
+    size_t prior = 0;
+};
+std::mutex g_l2_mutex;
+L2State g_l2[64];
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        (void)cudaGetLastError();
+        return -1;
+    }
+    return dev;
+}
+}  // namespace
+
+void note_persisting_l2(bool raised, size_t prior_limit) {
+    const int dev = current_device();
+    if (dev < 0) return;
+    std::lock_guard<std::mutex> lock(g_l2_mutex);
+    L2State &s = g_l2[dev];
+    s.windowed = true;
+    if (raised && !s.raised) {
+        s.raised = true;
+        s.prior = prior_limit;
+    }
+}
+
+void release_persisting_l2() {
+    const int dev = current_device();
+    if (dev < 0) return;
+    std::lock_guard<std::mutex> lock(g_l2_mutex);
+    L2State &s = g_l2[dev];
+    if (!s.windowed) return;
+    s.windowed = false;
+    if (cudaCtxResetPersistingL2Cache() != cudaSuccess) (void)cudaGetLastError();
+    if (s.raised) {
+        s.raised = false;
+        if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, s.prior) != cudaSuccess)
+            (void)cudaGetLastError();
+    }
+}
+
 int ensure_device_image(Code &c) { return ensure_device(c); }
 int set_error(int status, const std::string &msg) { return fail(status, msg); }
 }  // namespace qcmet

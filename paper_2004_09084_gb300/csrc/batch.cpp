@@ -15,6 +15,7 @@
 #include <string>
 #include <vector>
 
+#include "l2_persist.h"
 #include "qcmet_internal.h"
 #include "trace.h"
 
@@ -651,6 +652,7 @@ int qcmet_batch_create(const qcmet_frame *frames, int32_t K, int32_t iterations,
 int qcmet_batch_run(qcmet_batch *batch, void *stream) {
     if (!batch || !batch->exec) return qcmet::set_error(QCMET_ERR_INVALID_ARG, "batch must not be NULL");
     qcmet::TraceRange range("qcmet batch: %d frames x %d iterations", batch->K, batch->T);
+    qcmet::release_persisting_l2();
     cudaError_t e = cudaGraphLaunch(batch->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_err("cudaGraphLaunch", e);
     return QCMET_OK;

@@ -345,6 +345,44 @@ def test_l2_persist_window_changes_no_result(q, full):
     np.testing.assert_array_equal(p3, p[:3].cpu().numpy())
 
 
+def _persisting_l2_limit():
+    # the context's cudaLimitPersistingL2CacheSize, read through the CUDA runtime
+    import ctypes
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so.13"):
+        try:
+            rt = ctypes.CDLL(name)
+            break
+        except OSError:
+            continue
+    else:
+        pytest.skip("CUDA runtime library not found")
+    v = ctypes.c_size_t(0)
+    assert rt.cudaDeviceGetLimit(ctypes.byref(v), 0x06) == 0  # cudaLimitPersistingL2CacheSize
+    return v.value
+
+
+def test_windowed_decode_gives_l2_back_to_later_decodes(q, full):
+    # A frame-kernel decode under the persisting window raises the context's
+    # persisting-L2 limit; the next decode without a window puts it back, so
+    # the part of L2 set aside does not stay lost to the grouped kernel (with
+    # it set aside, grouped decodes of these frames ran about a quarter slower).
+    code, fr = full
+    qc = q.Code(code.base, code.shifts, code.Z)
+    d_llr = torch.from_numpy(fr.llr).cuda()
+    d_syn = torch.from_numpy(fr.syn).cuda()
+    q.decode(qc, d_llr, d_syn, 2, kernel="group")
+    torch.cuda.synchronize()
+    before = _persisting_l2_limit()
+    h, p, ok = q.decode(qc, d_llr, d_syn, 2, l2_persist=True, kernel="frame")
+    torch.cuda.synchronize()
+    assert _persisting_l2_limit() >= before
+    h2, p2, ok2 = q.decode(qc, d_llr, d_syn, 2, kernel="group")
+    torch.cuda.synchronize()
+    # back to the value found (the driver keeps the limit in steps of a few KiB)
+    assert abs(_persisting_l2_limit() - before) <= 1 << 20
+    assert torch.equal(h, h2) and torch.equal(p, p2) and torch.equal(ok, ok2)
+
+
 def test_maximum_size_frames(q):
     # The largest frame the boundary accepts, n = 4 Z = 2^31 - 4 (Z = 2^29 - 1,
     # odd, so rows end in a ragged pass), two frames so that frame offsets pass
