@@ -252,7 +252,9 @@ def decode(code: Code, llr, syn, iterations: int, hard=None, llr_post=None, ok=N
     Outputs are allocated when not given.  Returns ``(hard, llr_post, ok)``
     (``llr_post`` is None when ``want_post`` is false and none was passed).
     The call is asynchronous on ``stream`` (default: torch's current stream).
-    ``l2_persist`` keeps the core posteriors in a persisting L2 window.
+    ``l2_persist`` keeps the core posteriors in a persisting L2 window (frame
+    kernel only); the persisting-L2 limit it raises is put back before the
+    library's next decode without a window on that device.
     ``kernel`` is "auto", "frame" or "group" (``QCMET_KERNEL_*``); ``cluster``
     the grouped kernel's cluster size and ``groups`` its groups of four frames
     per cluster (0 = automatic).
